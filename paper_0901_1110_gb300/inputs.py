@@ -1,0 +1,155 @@
+"""Seeded synthetic workloads for the implicit radiation / ionization step.
+
+This module only draws inputs: grids, densities, initial states, point-source lists and the
+per-run settings.  It holds none of the method's arithmetic and imports neither the solver
+library nor the oracle; both sides consume what it returns.  The one conversion it does is the
+initial condition's own definition: the gas energy of a gas at temperature T0 and the given
+ionisation state (ideal gas, gamma = 5/3, as the workload is specified by T0).
+
+Workload recipes (the paper's test problems are idealised set-ups, not datasets):
+
+* ``uniform_h``      hydrogen only, uniform n_H, one central source split over the 8 cells
+                     around the centre (odd sizes: the centre cell); monochromatic 13.6 eV.
+* ``lognormal_hhe``  hydrogen + helium (Y = 0.24), lognormal n_H = nbar exp(s g - s^2 / 2)
+                     with g a unit-variance Gaussian random field of power spectrum
+                     P(k) ~ k^-2 (white noise filtered by k^-1 in Fourier space, k = 0
+                     removed), point sources at uniformly drawn cells with lognormal photon
+                     rates (median L50, log-sigma 1); T_B = 1e5 K blackbody spectrum.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+MPC = 3.0857e24      # cm
+KPC = 3.0857e21      # cm
+_KB = 1.380649e-16   # erg/K   (initial-condition conversion only)
+_MH = 1.67262192e-24 # g
+_EV = 1.602176634e-12
+
+
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    dx: float                   # comoving cell width, cm
+    ns: int                     # 1: H; 3: H + He
+    y_he: float                 # n_He / n_H
+    nH: np.ndarray              # (nz, ny, nx)
+    E: np.ndarray               # (nz, ny, nx) erg / cm^3
+    e: np.ndarray               # (nz, ny, nx) erg / g
+    n: np.ndarray               # (ns, nz, ny, nx) independent species HI[, HeI, HeII]
+    src_ijk: np.ndarray         # (nsrc, 3) cell indices (i, j, k)
+    src_rate: np.ndarray        # (nsrc,) photons / s
+    spectrum: tuple             # ("mono", photon energy erg) or ("blackbody", T_B)
+    dt: float
+    nsteps: int
+    a: float = 1.0
+    adot: float = 0.0
+    newton_tol: float = 1e-8
+    lin_tol: float = 1e-10
+    theta: float = 0.51
+    u_e: float = 1.0
+    u_n: float = 1.0
+    u_E: float = 1.0
+    bc: tuple = ("zero_flux",) * 6
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def N(self):
+        return self.nx * self.ny * self.nz
+
+    def state(self):
+        """Flat copies (x fastest) of the initial state: dict(E, e, n)."""
+        return dict(E=self.E.ravel().copy(), e=self.e.ravel().copy(),
+                    n=self.n.reshape(self.ns, -1).copy())
+
+
+def _gas_energy(T0, nH, nHe, nHII, nHeII, nHeIII):
+    """Specific energy of an ideal gas (gamma = 5/3) at T0 with the given ionisation."""
+    ne = nHII + nHeII + 2.0 * nHeIII
+    ntot = nH + nHe + ne
+    rho = _MH * (nH + 4.0 * nHe)
+    return 1.5 * _KB * T0 * ntot / rho
+
+
+def gaussian_random_field(shape, seed, slope=-2.0):
+    """Unit-variance Gaussian field with P(k) ~ k^slope (k = 0 mode removed)."""
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal(shape)
+    kz = np.fft.fftfreq(shape[0])[:, None, None]
+    ky = np.fft.fftfreq(shape[1])[None, :, None]
+    kx = np.fft.rfftfreq(shape[2])[None, None, :]
+    k = np.sqrt(kx * kx + ky * ky + kz * kz)
+    amp = np.zeros_like(k)
+    nz = k > 0
+    amp[nz] = k[nz] ** (slope / 2.0)
+    g = np.fft.irfftn(np.fft.rfftn(w) * amp, s=shape, axes=(0, 1, 2))
+    g -= g.mean()
+    return g / g.std()
+
+
+def uniform_h(n=32, box=1.0 * MPC, nH=1e-3, T0=100.0, x0=1e-4, E0=1e-20, ndot=5e48,
+              dt=1e12, nsteps=5, newton_tol=1e-8, lin_tol=1e-10, shape=None, name=None,
+              bc=("zero_flux",) * 6):
+    """Hydrogen-only uniform medium with a central source (the 32^3, 1 Mpc benchmark)."""
+    nz, ny, nx = shape if shape is not None else (n, n, n)
+    dx = box / nx
+    nHf = np.full((nz, ny, nx), nH)
+    nHII = x0 * nHf
+    n_sp = (nHf - nHII)[None]
+    z = np.zeros_like(nHf)
+    e = _gas_energy(T0, nHf, z, nHII, z, z)
+    # centre: the 8 cells around it for even sizes, the centre cell for odd sizes
+    cs = [[m // 2 - 1, m // 2] if m % 2 == 0 else [m // 2] for m in (nx, ny, nz)]
+    ijk = np.array([(i, j, k) for k in cs[2] for j in cs[1] for i in cs[0]])
+    rate = np.full(len(ijk), ndot / len(ijk))
+    return Workload(name=name or f"uniform_h_{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, dx=dx,
+                    ns=1, y_he=0.0, nH=nHf, E=np.full_like(nHf, E0), e=e, n=n_sp,
+                    src_ijk=ijk, src_rate=rate, spectrum=("mono", 13.6 * _EV), dt=dt,
+                    nsteps=nsteps, newton_tol=newton_tol, lin_tol=lin_tol,
+                    u_e=float(e.mean()), u_n=nH, u_E=E0, bc=tuple(bc))
+
+
+def lognormal_hhe(shape=(128, 128, 128), box=1.0 * MPC, seed=0, nbar=1e-3, sigma_ln=1.0,
+                  nsrc=16, L50=1e49, Y=0.24, T0=100.0, x0=1e-4, E0=1e-20, T_B=1e5, dt=5e12,
+                  nsteps=20, newton_tol=1e-8, lin_tol=1e-10, name=None,
+                  bc=("zero_flux",) * 6):
+    """Hydrogen + helium lognormal medium with seeded point sources (128^3 / 256^3 runs)."""
+    nz, ny, nx = shape
+    dx = box / nx
+    g = gaussian_random_field(shape, seed)
+    nH = nbar * np.exp(sigma_ln * g - 0.5 * sigma_ln ** 2)
+    y_he = Y / (4.0 * (1.0 - Y))
+    nHe = y_he * nH
+    nHII = x0 * nH
+    nHeII = x0 * nHe
+    nHeIII = 1e-4 * x0 * nHe
+    nHI = nH - nHII
+    nHeI = nHe - nHeII - nHeIII
+    e = _gas_energy(T0, nH, nHe, nHII, nHeII, nHeIII)
+    rng = np.random.default_rng(seed + 7919)
+    ijk = np.stack([rng.integers(0, nx, nsrc), rng.integers(0, ny, nsrc),
+                    rng.integers(0, nz, nsrc)], axis=1)
+    rate = L50 * np.exp(rng.standard_normal(nsrc))
+    return Workload(name=name or f"lognormal_hhe_{nx}x{ny}x{nz}_s{seed}", nx=nx, ny=ny, nz=nz,
+                    dx=dx, ns=3, y_he=y_he, nH=nH, E=np.full_like(nH, E0), e=e,
+                    n=np.stack([nHI, nHeI, nHeII]), src_ijk=ijk, src_rate=rate,
+                    spectrum=("blackbody", T_B), dt=dt, nsteps=nsteps, newton_tol=newton_tol,
+                    lin_tol=lin_tol, u_e=float(e.mean()), u_n=float(nH.mean()), u_E=E0,
+                    bc=tuple(bc))
+
+
+# the named benchmark workloads ----------------------------------------------------------------
+
+def config_uniform_32():
+    """Plain FP64 method: 32^3, 1 Mpc, H only, n_H = 1e-3, T0 = 100 K, x_HII = 1e-4, one
+    central 5e48 s^-1 source at 13.6 eV, zero-flux boundaries, a = 1, 5 steps of 1e12 s."""
+    return uniform_h(32, name="uniform_h_32")
+
+
+def config_lognormal(n=128, nsrc=16, seed=0):
+    """H + He lognormal medium (sigma_ln = 1, P(k) ~ k^-2, mean n_H = 1e-3), lognormal point
+    sources (median 1e49 s^-1), 20 steps of 5e12 s; 128^3 with 16 sources or 256^3 with 64."""
+    return lognormal_hhe((n, n, n), seed=seed, nsrc=nsrc, name=f"lognormal_hhe_{n}")
