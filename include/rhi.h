@@ -1,0 +1,180 @@
+/*
+ * rhi.h -- C ABI of the GB300 implicit radiation / ionization / gas-energy step.
+ *
+ * One call of rhi_implicit_step advances the coupled system of Reynolds, Hayes, Paschos &
+ * Norman (Sec. 3.1, eqs. RT-cons_energy, RT-chemical_ionization, RT-cons_radiation)
+ *
+ *     d e_c / dt = -2 (adot/a) e_c + G - Lambda
+ *     d n_i / dt = alpha_ij n_e n_j - n_i Gamma_i
+ *     d E   / dt = div(D grad E) - m (adot/a) E + 4 pi eta - c kappa E
+ *
+ * by one theta-scheme step (Sec. 3.2, eqs. energy/chemistry/radiation_simplified), solving the
+ * nonlinear residual f(U) = 0 (eq. nonlinear_residual) with a globalised inexact Newton
+ * iteration (Sec. 3.2), a cell-local Schur-complement elimination of the (e_c, n_i) blocks
+ * (Sec. 3.2.1, eqs. newton_system2, schur_components, step_ia) and a multigrid-preconditioned
+ * conjugate-gradient solve of the remaining 7-point system in E (Sec. 3.2.1, step (ii)).
+ *
+ * Conventions for every entry point:
+ *  - Fields are cell-centred on an nx x ny x nz grid, flat index i + nx*(j + ny*k) (x fastest),
+ *    FP64, CGS units, comoving (Sec. 2: n_i, E comoving; e specific energy in erg/g).
+ *  - "n" arrays hold the independent species back to back: n_HI for n_species = 1, then
+ *    n_HeI, n_HeII for n_species = 3 (n_species * N doubles).  n_HII, n_HeIII and n_e follow
+ *    from element conservation (n_He = y_he * n_H).
+ *  - Pointers flagged on_device = 1 are CUDA device pointers on the handle's device; 0 means
+ *    host memory.  The library copies inputs and never keeps caller pointers; the caller owns
+ *    all memory it passes.  Device work runs on the stream given to rhi_create; calls return
+ *    after that work has completed.
+ *  - Every function returns RHI_OK (0) or an RHI_ERR_* code; rhi_last_error(handle) gives a
+ *    one-line reason.  On a failed rhi_implicit_step the state is left at U^n.
+ */
+#ifndef RHI_H
+#define RHI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RHI_OK 0
+#define RHI_ERR_ARG 1           /* invalid argument or size                                  */
+#define RHI_ERR_CUDA 2          /* a CUDA call failed                                        */
+#define RHI_ERR_NONCONVERGED 3  /* Newton did not reach newton_tol within max_newton         */
+#define RHI_ERR_NONPHYSICAL 4   /* non-positive or non-finite state, or a CG breakdown       */
+#define RHI_ERR_STATE 5         /* call order: no state set yet                              */
+
+enum { RHI_BC_ZERO_FLUX = 0, RHI_BC_PERIODIC = 1 };
+enum { RHI_GUESS_PREVIOUS = 0, RHI_GUESS_PREDICTOR = 1, RHI_GUESS_LEARNED = 2 };
+enum { RHI_PRECOND_JACOBI = 0, RHI_PRECOND_MG_FP64 = 1, RHI_PRECOND_MG_FP32 = 2 };
+enum { RHI_SPECTRUM_MONO = 0, RHI_SPECTRUM_BLACKBODY = 1, RHI_SPECTRUM_POWERLAW = 2 };
+
+/* Uniform Cartesian grid (Sec. 1: uniform grids only); dx = comoving cell width in cm. */
+typedef struct {
+    int nx, ny, nz;
+    double dx;
+} rhi_grid;
+
+/* Boundary kind per face, order x-, x+, y-, y+, z-, z+; periodic faces come in pairs. */
+typedef struct {
+    int kind[6];
+} rhi_bc;
+
+/* Method and closure parameters.  Fill with rhi_params_default, then override. */
+typedef struct {
+    int n_species;          /* 1: H (HI); 3: H + He (HI, HeI, HeII)                          */
+    double y_he;            /* n_He / n_H; 0 when n_species = 1                              */
+    double theta;           /* theta of the two-level scheme (Sec. 3.2)                      */
+    int m_grey;             /* m of eq. cons_radiation (1 grey, 0 monochromatic)             */
+    int isothermal;         /* 1: temperature held at its value at rhi_set_state; e_c = 0    */
+    int limiter;            /* 1: eq. limiter; 0: D = c / (3 max(kappa, kappa_floor))         */
+    double kappa_floor;     /* cm^-1, only without the limiter                               */
+    double u_e, u_n, u_E;   /* scalings of eq. scalings: erg/g, cm^-3, erg/cm^3               */
+    double tau;             /* fraction-to-boundary of the positivity cap (0 < tau < 1)      */
+    double lam_min;         /* smallest line-search parameter                                */
+    int max_newton;         /* Newton iterations per step                                    */
+    int max_pcg;            /* CG iterations per Newton iteration                            */
+    int guess;              /* RHI_GUESS_*                                                   */
+    int precond;            /* RHI_PRECOND_*                                                 */
+    int mg_levels;          /* multigrid levels including the finest                         */
+    int mg_pre, mg_post;    /* weighted-Jacobi sweeps before / after the coarse correction   */
+    int mg_coarse_sweeps;   /* weighted-Jacobi sweeps on the coarsest level                  */
+    double mg_omega;        /* Jacobi weight                                                 */
+    /* grey constants per absorber (HI, HeI, HeII) of eq. adaptive_spectrum:
+       kappa = sum sk_X n_X / a^3, Gamma_X = c pgam_X E / a^3, G = c E sum ph_X n_X / (a^3 rho) */
+    double sk[3], pgam[3], ph[3];
+    double photon_energy;   /* mean photon energy (erg) used by rhi_set_sources              */
+} rhi_params;
+
+typedef struct {
+    int status;             /* RHI_OK or the error of the last step                          */
+    int newton_its;         /* Newton iterations of the last step                            */
+    int pcg_its;            /* CG iterations summed over the step                            */
+    int vcycles;            /* preconditioner applications summed over the step              */
+    int backtracks;         /* line-search halvings                                          */
+    int full_steps;         /* line searches that fell back to the full step                 */
+    int guess_used;         /* RHI_GUESS_* actually used (learned falls back to previous)    */
+    int launches;           /* kernel launches of the last step                              */
+    double res_initial;     /* ||f(U_0)|| (eq. rmsnorm, scaled)                              */
+    double res_final;       /* ||f(U^{n+1})||                                                */
+    double res_guess_prev;  /* ||f(U^n)|| when a learned guess was tried, else 0             */
+    double ms;              /* device time of the last step, ms                              */
+} rhi_stats;
+
+typedef struct rhi_ctx* rhi_handle;
+
+/* Defaults: theta 0.51 (Sec. 3.2), limiter on, tau 0.99, lam_min 1/16, max_newton 50,
+   max_pcg 200, previous-step guess, FP64 multigrid with 6 levels, 2 + 2 sweeps, 16 coarse
+   sweeps, omega 0.8, scalings 1, and the grey constants of 13.6 eV monochromatic radiation
+   with a 6.3e-18 cm^2 HI cross section.  n_species must be 1 or 3. */
+int rhi_params_default(rhi_params* p, int n_species);
+
+/* Grey constants of eq. adaptive_spectrum (Sec. 3.2.5) for an assumed spectrum chi(nu):
+   RHI_SPECTRUM_MONO (param = photon energy, erg), RHI_SPECTRUM_BLACKBODY (param = T_B, K),
+   RHI_SPECTRUM_POWERLAW (chi ~ nu^param, param < -1).  Cross sections are
+   sigma_X (nu / nu_X)^-3 above thresholds 13.6 / 24.6 / 54.4 eV with sigma_X = 6.30e-18,
+   7.42e-18, 1.575e-18 cm^2; integrals run from 13.6 eV up (eq. grey_definition).  Writes
+   sk, pgam, ph (3 each; absorbers beyond n_species are 0) and the mean photon energy.
+   Host computation only. */
+int rhi_grey_constants(int spectrum, double param, int n_species, double* sk, double* pgam,
+                       double* ph, double* photon_energy);
+
+/* Creates a solver for one grid on the current CUDA device.  stream is a cudaStream_t (NULL:
+   the legacy default stream).  Allocates every device buffer the step needs.  Errors:
+   RHI_ERR_ARG for non-positive sizes, unpaired periodic faces, n_species not 1 or 3, or
+   out-of-range parameters; RHI_ERR_CUDA when allocation fails. */
+int rhi_create(const rhi_grid* grid, const rhi_bc* bc, const rhi_params* params,
+               void* stream, rhi_handle* out);
+
+/* Sets the state U^n: E (N), e (N, specific gas energy), n (n_species * N), the comoving
+   hydrogen density n_H (N) and the emissivity 4 pi eta (N, erg cm^-3 s^-1; NULL = 0).
+   Requires E > 0, e > 0, n_H > 0 and every species (independent and derived) >= 0
+   (RHI_ERR_NONPHYSICAL otherwise).  Isothermal runs fix the temperature here. */
+int rhi_set_state(rhi_handle h, const double* E, const double* e, const double* n,
+                  const double* n_H, const double* src, int on_device);
+
+/* Adds point sources to the emissivity: source s puts photons_per_s[s] * photon_energy into
+   the comoving volume dx^3 of cell (ijk[3s], ijk[3s+1], ijk[3s+2]).  Host arrays. */
+int rhi_set_sources(rhi_handle h, int nsrc, const int* ijk, const double* photons_per_s);
+
+/* One implicit step t^n -> t^n + dt at expansion factor a and adot = da/dt (both time
+   levels use them).  newton_tol is epsilon of Sec. 3.2 (||f|| of eq. rmsnorm over scaled
+   unknowns); lin_tol sets the inexact-Newton tolerance delta_k = lin_tol * ||f(U_k)||. */
+int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double newton_tol,
+                      double lin_tol);
+
+/* Copies the current state out (E, e, n as in rhi_set_state). */
+int rhi_get_state(rhi_handle h, double* E, double* e, double* n, int on_device);
+
+/* Statistics of the last rhi_implicit_step. */
+int rhi_get_stats(rhi_handle h, rhi_stats* out);
+
+/* The first Newton linear system of a step from the current state with the previous-step
+   guess (U_0 = U^n), without solving it: the scaled residual f (n_species + 2 blocks of N:
+   e_c, n_1.., E; eq. nonlinear_residual divided by the scalings), the Schur matrix diagonal
+   S_diag (N), its off-diagonal face weights S_face (3 blocks of N: the face between a cell and
+   its -x, -y, -z neighbour, as a positive number; the matrix entry is its negative; 0 on
+   zero-flux boundary faces) and the Schur right-hand side rhs = L M^-1 f_M - f_E (N), all in
+   scaled unknowns.  Any output pointer may be NULL. */
+int rhi_linearize(rhi_handle h, double dt, double a, double adot, double* f, double* S_diag,
+                  double* S_face, double* rhs, int on_device);
+
+/* Applies the configured preconditioner (one V-cycle or Jacobi) of the Schur matrix built by
+   the last rhi_linearize to r (N), writing z (N). */
+int rhi_precond_apply(rhi_handle h, const double* r, double* z, int on_device);
+
+/* Per-kernel device time: with profiling on, every launch is bracketed by CUDA events on the
+   handle's stream and accumulated per kernel name.  rhi_kernel_times writes up to max
+   entries (names as NUL-terminated strings of at most 47 chars in names[48*i..], total ms,
+   launch count) and returns the number of kernels (>= 0) or -RHI_ERR_*. */
+int rhi_set_profiling(rhi_handle h, int on);
+int rhi_kernel_times(rhi_handle h, int max, char* names, double* total_ms, int* launches);
+
+const char* rhi_last_error(rhi_handle h);
+const char* rhi_status_string(int status);
+void rhi_destroy(rhi_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RHI_H */

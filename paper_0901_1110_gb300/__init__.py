@@ -1,1 +1,268 @@
-"""GB300-native implicit radiation / ionization / gas-energy step (placeholder; binding follows)."""
+"""Python binding of librhi, the GB300 implicit radiation / ionization / gas-energy step.
+
+Argument marshalling only: every step of the solve runs in the library's CUDA kernels.  The
+functions keep the C names of ``include/rhi.h``; ``Solver`` wraps one handle.  Importing this
+package does not load the library; the first call does, and fails loudly when ``librhi.so``
+has not been built (``paper_0901_1110_gb300._build.build()``).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librhi.so")
+
+RHI_OK, RHI_ERR_ARG, RHI_ERR_CUDA, RHI_ERR_NONCONVERGED, RHI_ERR_NONPHYSICAL, RHI_ERR_STATE = range(6)
+RHI_BC_ZERO_FLUX, RHI_BC_PERIODIC = 0, 1
+RHI_GUESS_PREVIOUS, RHI_GUESS_PREDICTOR, RHI_GUESS_LEARNED = 0, 1, 2
+RHI_PRECOND_JACOBI, RHI_PRECOND_MG_FP64, RHI_PRECOND_MG_FP32 = 0, 1, 2
+RHI_SPECTRUM_MONO, RHI_SPECTRUM_BLACKBODY, RHI_SPECTRUM_POWERLAW = 0, 1, 2
+
+
+class rhi_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double)]
+
+
+class rhi_bc(C.Structure):
+    _fields_ = [("kind", C.c_int * 6)]
+
+
+class rhi_params(C.Structure):
+    _fields_ = [("n_species", C.c_int), ("y_he", C.c_double), ("theta", C.c_double),
+                ("m_grey", C.c_int), ("isothermal", C.c_int), ("limiter", C.c_int),
+                ("kappa_floor", C.c_double), ("u_e", C.c_double), ("u_n", C.c_double),
+                ("u_E", C.c_double), ("tau", C.c_double), ("lam_min", C.c_double),
+                ("max_newton", C.c_int), ("max_pcg", C.c_int), ("guess", C.c_int),
+                ("precond", C.c_int), ("mg_levels", C.c_int), ("mg_pre", C.c_int),
+                ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double),
+                ("sk", C.c_double * 3), ("pgam", C.c_double * 3), ("ph", C.c_double * 3),
+                ("photon_energy", C.c_double)]
+
+
+class rhi_stats(C.Structure):
+    _fields_ = [("status", C.c_int), ("newton_its", C.c_int), ("pcg_its", C.c_int),
+                ("vcycles", C.c_int), ("backtracks", C.c_int), ("full_steps", C.c_int),
+                ("guess_used", C.c_int), ("launches", C.c_int), ("res_initial", C.c_double),
+                ("res_final", C.c_double), ("res_guess_prev", C.c_double), ("ms", C.c_double)]
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_SIGS = {
+    "rhi_params_default": (C.c_int, [C.POINTER(rhi_params), C.c_int]),
+    "rhi_grey_constants": (C.c_int, [C.c_int, C.c_double, C.c_int, _D, _D, _D, _D]),
+    "rhi_create": (C.c_int, [C.POINTER(rhi_grid), C.POINTER(rhi_bc), C.POINTER(rhi_params), _P,
+                             C.POINTER(_P)]),
+    "rhi_set_state": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int]),
+    "rhi_set_sources": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), _D]),
+    "rhi_implicit_step": (C.c_int, [_P, C.c_double, C.c_double, C.c_double, C.c_double,
+                                    C.c_double]),
+    "rhi_get_state": (C.c_int, [_P, _P, _P, _P, C.c_int]),
+    "rhi_get_stats": (C.c_int, [_P, C.POINTER(rhi_stats)]),
+    "rhi_linearize": (C.c_int, [_P, C.c_double, C.c_double, C.c_double, _P, _P, _P, _P, C.c_int]),
+    "rhi_precond_apply": (C.c_int, [_P, _P, _P, C.c_int]),
+    "rhi_set_profiling": (C.c_int, [_P, C.c_int]),
+    "rhi_kernel_times": (C.c_int, [_P, C.c_int, C.c_char_p, _D, C.POINTER(C.c_int)]),
+    "rhi_last_error": (C.c_char_p, [_P]),
+    "rhi_status_string": (C.c_char_p, [C.c_int]),
+    "rhi_destroy": (None, [_P]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded librhi.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_0901_1110_gb300._build.build() (needs nvcc)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class RhiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+# ---- C functions under their own names ---------------------------------------------------------
+
+def rhi_params_default(n_species):
+    p = rhi_params()
+    rc = lib().rhi_params_default(C.byref(p), n_species)
+    if rc:
+        raise RhiError(rc, "rhi_params_default")
+    return p
+
+
+def rhi_grey_constants(spectrum, param, n_species):
+    sk, pg, ph = (C.c_double * 3)(), (C.c_double * 3)(), (C.c_double * 3)()
+    eps = C.c_double()
+    rc = lib().rhi_grey_constants(spectrum, param, n_species, sk, pg, ph, C.byref(eps))
+    if rc:
+        raise RhiError(rc, "rhi_grey_constants")
+    return dict(sk=np.array(sk[:]), pgam=np.array(pg[:]), ph=np.array(ph[:]), eps=eps.value)
+
+
+def rhi_status_string(code):
+    return lib().rhi_status_string(code).decode()
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or a CUDA tensor (float64, contiguous)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("arrays must be C-contiguous float64")
+        return a.ctypes.data, 0
+    # torch tensor
+    if a.dtype.__str__() != "torch.float64" or not a.is_contiguous():
+        raise TypeError("tensors must be contiguous float64")
+    return a.data_ptr(), (1 if a.is_cuda else 0)
+
+
+class Solver:
+    """One rhi handle: grid, boundaries and parameters fixed at creation."""
+
+    def __init__(self, nx, ny, nz, dx, params, bc=(RHI_BC_ZERO_FLUX,) * 6, stream=None):
+        self.grid = rhi_grid(nx, ny, nz, dx)
+        b = rhi_bc()
+        for q in range(6):
+            b.kind[q] = int(bc[q])
+        self.bc = b
+        self.params = params
+        self.ns = params.n_species
+        self.N = nx * ny * nz
+        h = C.c_void_p()
+        rc = lib().rhi_create(C.byref(self.grid), C.byref(b), C.byref(params),
+                              C.c_void_p(stream or 0), C.byref(h))
+        if rc:
+            raise RhiError(rc, "rhi_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.rhi_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what, check=True):
+        if rc and check:
+            raise RhiError(rc, f"{what}: {lib().rhi_last_error(self.h).decode()}")
+        return rc
+
+    def set_state(self, E, e, n, nH, src=None):
+        (pE, d0), (pe, d1), (pn, d2), (pH, d3) = _ptr(E), _ptr(e), _ptr(n), _ptr(nH)
+        ps, d4 = _ptr(src)
+        devs = {d0, d1, d2, d3} | ({d4} if src is not None else set())
+        if len(devs) != 1:
+            raise TypeError("all fields on the host or all on the device")
+        return self._check(lib().rhi_set_state(self.h, pE, pe, pn, pH, ps, d0), "rhi_set_state")
+
+    def set_sources(self, ijk, rate):
+        ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+        rate = np.ascontiguousarray(rate, dtype=np.float64).ravel()
+        return self._check(lib().rhi_set_sources(
+            self.h, len(rate), ijk.ctypes.data_as(C.POINTER(C.c_int)),
+            rate.ctypes.data_as(_D)), "rhi_set_sources")
+
+    def step(self, dt, a=1.0, adot=0.0, newton_tol=1e-8, lin_tol=1e-10, check=True):
+        return self._check(lib().rhi_implicit_step(self.h, dt, a, adot, newton_tol, lin_tol),
+                           "rhi_implicit_step", check)
+
+    def get_state(self, E=None, e=None, n=None):
+        """Host copies (numpy) unless device tensors are given to fill."""
+        if E is None:
+            E = np.empty(self.N)
+            e = np.empty(self.N)
+            n = np.empty(self.ns * self.N)
+        (pE, dev), (pe, _), (pn, _) = _ptr(E), _ptr(e), _ptr(n)
+        self._check(lib().rhi_get_state(self.h, pE, pe, pn, dev), "rhi_get_state")
+        return dict(E=E, e=e, n=n.reshape(self.ns, self.N) if isinstance(n, np.ndarray) else n)
+
+    def stats(self):
+        s = rhi_stats()
+        lib().rhi_get_stats(self.h, C.byref(s))
+        return {k: getattr(s, k) for k, _ in rhi_stats._fields_}
+
+    def linearize(self, dt, a=1.0, adot=0.0):
+        nv = self.ns + 2
+        f = np.empty(nv * self.N)
+        d = np.empty(self.N)
+        fc = np.empty(3 * self.N)
+        r = np.empty(self.N)
+        self._check(lib().rhi_linearize(self.h, dt, a, adot, f.ctypes.data, d.ctypes.data,
+                                        fc.ctypes.data, r.ctypes.data, 0), "rhi_linearize")
+        return dict(f=f.reshape(nv, self.N), diag=d, face=fc.reshape(3, self.N), rhs=r)
+
+    def precond_apply(self, r):
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        z = np.empty_like(r)
+        self._check(lib().rhi_precond_apply(self.h, r.ctypes.data, z.ctypes.data, 0),
+                    "rhi_precond_apply")
+        return z
+
+    def set_profiling(self, on):
+        return self._check(lib().rhi_set_profiling(self.h, int(on)), "rhi_set_profiling")
+
+    def kernel_times(self):
+        n = lib().rhi_kernel_times(self.h, 0, None, None, None)
+        if n <= 0:
+            return {}
+        names = C.create_string_buffer(48 * n)
+        ms = (C.c_double * n)()
+        cnt = (C.c_int * n)()
+        lib().rhi_kernel_times(self.h, n, names, ms, cnt)
+        raw = names.raw
+        return {raw[48 * i:48 * i + 48].split(b"\0")[0].decode(): (ms[i], cnt[i]) for i in range(n)}
+
+
+def params_for_workload(w, **overrides):
+    """rhi_params for a synthetic workload (inputs.Workload): species, scalings, theta and the
+    grey constants the library computes for the workload's spectrum."""
+    p = rhi_params_default(w.ns)
+    p.y_he = w.y_he
+    p.theta = w.theta
+    p.u_e, p.u_n, p.u_E = w.u_e, w.u_n, w.u_E
+    kind, par = w.spectrum
+    spec = {"mono": RHI_SPECTRUM_MONO, "blackbody": RHI_SPECTRUM_BLACKBODY,
+            "powerlaw": RHI_SPECTRUM_POWERLAW}[kind]
+    g = rhi_grey_constants(spec, par, w.ns)
+    for X in range(3):
+        p.sk[X], p.pgam[X], p.ph[X] = g["sk"][X], g["pgam"][X], g["ph"][X]
+    p.photon_energy = g["eps"]
+    for k, v in overrides.items():
+        if k in ("sk", "pgam", "ph"):
+            for X in range(3):
+                getattr(p, k)[X] = v[X]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def solver_for_workload(w, stream=None, sources=True, **overrides):
+    """A Solver holding the workload's initial state and point sources (host marshalling)."""
+    p = params_for_workload(w, **overrides)
+    bc = [RHI_BC_PERIODIC if b == "periodic" else RHI_BC_ZERO_FLUX for b in w.bc]
+    s = Solver(w.nx, w.ny, w.nz, w.dx, p, bc=bc, stream=stream)
+    st = w.state()
+    s.set_state(st["E"], st["e"], np.ascontiguousarray(st["n"]).ravel(),
+                np.ascontiguousarray(w.nH.ravel()))
+    if sources and len(w.src_rate):
+        s.set_sources(w.src_ijk, w.src_rate)
+    return s

@@ -1,0 +1,838 @@
+// Host orchestration of the implicit step behind the C ABI (include/rhi.h): buffers, the
+// globalised inexact Newton iteration (Sec. 3.2), the Schur-system CG solve with its
+// multigrid preconditioner (Sec. 3.2.1, step (ii)), profiling and statistics.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "rhi_linear.cuh"
+
+using namespace rhi;
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// launch hook: counts launches, and with profiling on brackets each one with CUDA events
+
+struct Profiler : LaunchHook {
+    cudaStream_t st = nullptr;
+    bool on = false;
+    int launches = 0;
+    std::vector<cudaEvent_t> pool;
+    struct Rec { const char* name; cudaEvent_t a, b; };
+    std::vector<Rec> pending;
+    std::map<std::string, std::pair<double, int>> acc;
+    const char* cur = nullptr;
+    cudaEvent_t cur_a = nullptr;
+
+    cudaEvent_t get() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void begin(const char* name) override {
+        ++launches;
+        if (!on) return;
+        cur = name;
+        cur_a = get();
+        cudaEventRecord(cur_a, st);
+    }
+    void end() override {
+        if (!on || !cur) return;
+        cudaEvent_t b = get();
+        cudaEventRecord(b, st);
+        pending.push_back({cur, cur_a, b});
+        cur = nullptr;
+    }
+    void resolve() {
+        for (auto& r : pending) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(r.b) == cudaSuccess) cudaEventElapsedTime(&ms, r.a, r.b);
+            auto& v = acc[r.name];
+            v.first += ms;
+            v.second += 1;
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        pending.clear();
+    }
+    ~Profiler() override {
+        for (auto& r : pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+template <typename T>
+struct Level {
+    int nx = 0, ny = 0, nz = 0;
+    long long N = 0;
+    T* diag = nullptr;
+    T* W[3] = {nullptr, nullptr, nullptr};
+    T* b = nullptr;
+    T* x = nullptr;
+    T* xt = nullptr;
+};
+
+}  // namespace
+
+struct rhi_ctx {
+    rhi_grid grid{};
+    rhi_bc bc{};
+    rhi_params prm{};
+    int ns = 1, nv = 3, nm = 2;
+    long long N = 0;
+    int per[3] = {0, 0, 0};
+    cudaStream_t st = nullptr;
+    std::string err;
+    rhi_stats stats{};
+    Profiler prof;
+    bool have_state = false;
+    bool have_linear = false;
+
+    std::vector<void*> allocs;
+
+    // state U^n
+    double *E_s = nullptr, *e_s = nullptr, *n_s = nullptr, *nH = nullptr, *src = nullptr,
+           *Tiso = nullptr;
+    // two work iterates, contiguous (e_c | n_1 .. | E), their opacity and face coefficients
+    double* U[2] = {nullptr, nullptr};
+    double* kap[2] = {nullptr, nullptr};
+    double* W[2] = {nullptr, nullptr};
+    double* g = nullptr;
+    double *diag[2] = {nullptr, nullptr}, *rhs[2] = {nullptr, nullptr};
+    double *fMt[2] = {nullptr, nullptr}, *MiU[2] = {nullptr, nullptr};
+    double* f_tmp = nullptr;
+    // CG
+    double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+    double* partials = nullptr;
+    double* scal = nullptr;
+    double* h_scal = nullptr;   // pinned
+    int* d_flag = nullptr;
+    double2* table = nullptr;
+    // multigrid
+    std::vector<Level<double>> mg64;
+    std::vector<Level<float>> mg32;
+    // operator the preconditioner was set up for
+    Op<double> op0{};
+
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+int fail(rhi_ctx* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(h, RHI_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+int dalloc(rhi_ctx* h, T** p, size_t count) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return fail(h, RHI_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    h->allocs.push_back(v);
+    *p = (T*)v;
+    return RHI_OK;
+}
+
+StepParams make_params(const rhi_ctx* h, double dt, double a, double adot) {
+    StepParams P{};
+    P.nx = h->grid.nx; P.ny = h->grid.ny; P.nz = h->grid.nz;
+    P.N = h->N;
+    P.per_x = h->per[0]; P.per_y = h->per[1]; P.per_z = h->per[2];
+    P.dx = h->grid.dx;
+    P.a = a; P.ia3 = 1.0 / (a * a * a); P.adot_a = adot / a;
+    P.dt = dt; P.dth = dt * h->prm.theta; P.dtm1 = dt * (h->prm.theta - 1.0);
+    P.inv_adx = 1.0 / (a * h->grid.dx);
+    P.inv_a2dx2 = P.inv_adx * P.inv_adx;
+    const int nmax = std::max(h->grid.nx, std::max(h->grid.ny, h->grid.nz));
+    P.R_min = 1.0 / (a * nmax * h->grid.dx);
+    P.kappa_floor = h->prm.kappa_floor;
+    P.m_grey = (double)h->prm.m_grey;
+    P.isothermal = h->prm.isothermal; P.limiter = h->prm.limiter;
+    P.y_he = h->prm.y_he;
+    P.u_e = h->prm.u_e; P.u_n = h->prm.u_n; P.u_E = h->prm.u_E;
+    P.iu_e = 1.0 / P.u_e; P.iu_n = 1.0 / P.u_n; P.iu_E = 1.0 / P.u_E;
+    for (int X = 0; X < 3; ++X) { P.sk[X] = h->prm.sk[X]; P.pg[X] = h->prm.pgam[X]; P.ph[X] = h->prm.ph[X]; }
+    P.tau = h->prm.tau;
+    P.table = h->table;
+    return P;
+}
+
+// names of the physics kernels for the profiler
+struct Scope {
+    Profiler& p;
+    Scope(Profiler& pr, const char* n) : p(pr) { p.begin(n); }
+    ~Scope() { p.end(); }
+};
+
+int read_scalar(rhi_ctx* h, int slot, double* out) {
+    CK(cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double) * S_NSCAL, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    *out = h->h_scal[slot];
+    return RHI_OK;
+}
+
+// ||f||_RMS from the cell kernel's partials
+int residual_norm(rhi_ctx* h, int nparts, double* out) {
+    LinLaunch L(h->st, &h->prof);
+    CK(L.reduce(h->partials, nparts, h->scal, RED_SUM, S_TMP));
+    double s;
+    int rc = read_scalar(h, S_TMP, &s);
+    if (rc) return rc;
+    *out = std::sqrt(s / ((double)h->N * h->nv));
+    return RHI_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// multigrid
+
+void level_dims(int n, int& c) { c = (n + 1) / 2; }
+
+int mg_build_levels(rhi_ctx* h) {
+    const int L = std::max(1, h->prm.mg_levels);
+    int nx = h->grid.nx, ny = h->grid.ny, nz = h->grid.nz;
+    std::vector<int> dims;
+    for (int l = 0; l < L; ++l) {
+        dims.push_back(nx); dims.push_back(ny); dims.push_back(nz);
+        if (nx == 1 && ny == 1 && nz == 1) break;
+        int cx, cy, cz;
+        level_dims(nx, cx); level_dims(ny, cy); level_dims(nz, cz);
+        nx = cx; ny = cy; nz = cz;
+    }
+    const int nl = (int)dims.size() / 3;
+    if (h->prm.precond == RHI_PRECOND_MG_FP64) {
+        h->mg64.resize(nl);
+        for (int l = 0; l < nl; ++l) {
+            auto& v = h->mg64[l];
+            v.nx = dims[3 * l]; v.ny = dims[3 * l + 1]; v.nz = dims[3 * l + 2];
+            v.N = (long long)v.nx * v.ny * v.nz;
+            int rc;
+            if (l > 0) {
+                if ((rc = dalloc(h, &v.diag, v.N))) return rc;
+                for (int a = 0; a < 3; ++a) if ((rc = dalloc(h, &v.W[a], v.N))) return rc;
+                if ((rc = dalloc(h, &v.b, v.N))) return rc;
+                if ((rc = dalloc(h, &v.x, v.N))) return rc;
+            }
+            if ((rc = dalloc(h, &v.xt, v.N))) return rc;
+        }
+    } else if (h->prm.precond == RHI_PRECOND_MG_FP32) {
+        h->mg32.resize(nl);
+        for (int l = 0; l < nl; ++l) {
+            auto& v = h->mg32[l];
+            v.nx = dims[3 * l]; v.ny = dims[3 * l + 1]; v.nz = dims[3 * l + 2];
+            v.N = (long long)v.nx * v.ny * v.nz;
+            int rc;
+            if ((rc = dalloc(h, &v.diag, v.N))) return rc;
+            for (int a = 0; a < 3; ++a) if ((rc = dalloc(h, &v.W[a], v.N))) return rc;
+            if ((rc = dalloc(h, &v.b, v.N))) return rc;
+            if ((rc = dalloc(h, &v.x, v.N))) return rc;
+            if ((rc = dalloc(h, &v.xt, v.N))) return rc;
+        }
+    }
+    return RHI_OK;
+}
+
+template <typename T>
+Op<T> level_op(const rhi_ctx* h, const Level<T>& v) {
+    Op<T> A{};
+    A.nx = v.nx; A.ny = v.ny; A.nz = v.nz; A.N = v.N;
+    for (int a = 0; a < 3; ++a) { A.per[a] = h->per[a]; A.W[a] = v.W[a]; }
+    A.diag = v.diag;
+    A.scale = T(1);
+    return A;
+}
+
+// coarse operators for the current finest operator h->op0
+int precond_setup(rhi_ctx* h) {
+    LinLaunch L(h->st, &h->prof);
+    if (h->prm.precond == RHI_PRECOND_MG_FP64) {
+        auto& lv = h->mg64;
+        for (size_t l = 0; l + 1 < lv.size(); ++l) {
+            Op<double> A = (l == 0) ? h->op0 : level_op(h, lv[l]);
+            auto& c = lv[l + 1];
+            CK((L.coarsen<double, double>(A, c.nx, c.ny, c.nz, c.diag, c.W[0], c.W[1], c.W[2])));
+            CK(L.diag_faces<double>(level_op(h, c), c.diag));
+        }
+    } else if (h->prm.precond == RHI_PRECOND_MG_FP32) {
+        auto& lv = h->mg32;
+        CK(L.cast_op(h->op0, lv[0].diag, lv[0].W[0], lv[0].W[1], lv[0].W[2]));
+        for (size_t l = 0; l + 1 < lv.size(); ++l) {
+            auto& c = lv[l + 1];
+            if (l == 0)
+                CK((L.coarsen<double, float>(h->op0, c.nx, c.ny, c.nz, c.diag, c.W[0], c.W[1], c.W[2])));
+            else
+                CK((L.coarsen<float, float>(level_op(h, lv[l]), c.nx, c.ny, c.nz, c.diag, c.W[0], c.W[1], c.W[2])));
+            CK(L.diag_faces<float>(level_op(h, c), c.diag));
+        }
+    }
+    return RHI_OK;
+}
+
+// one V-cycle on levels l.. with right-hand side lv[l].b; result in lv[l].x
+template <typename T>
+int vcycle(rhi_ctx* h, std::vector<Level<T>>& lv, size_t l, const Op<T>& A0) {
+    LinLaunch L(h->st, &h->prof);
+    Level<T>& v = lv[l];
+    const Op<T> A = (l == 0) ? A0 : level_op(h, v);
+    const T om = (T)h->prm.mg_omega;
+    if (l + 1 == lv.size()) {
+        CK(L.smooth<T>(A, v.b, v.x, v.x, om, 1));
+        for (int s = 1; s < h->prm.mg_coarse_sweeps; ++s) {
+            CK(L.smooth<T>(A, v.b, v.x, v.xt, om, 0));
+            std::swap(v.x, v.xt);
+        }
+        return RHI_OK;
+    }
+    CK(L.smooth<T>(A, v.b, v.x, v.x, om, 1));
+    for (int s = 1; s < h->prm.mg_pre; ++s) {
+        CK(L.smooth<T>(A, v.b, v.x, v.xt, om, 0));
+        std::swap(v.x, v.xt);
+    }
+    Level<T>& c = lv[l + 1];
+    CK(L.restrict_res<T>(A, v.b, v.x, c.nx, c.ny, c.nz, c.b));
+    int rc = vcycle<T>(h, lv, l + 1, A0);
+    if (rc) return rc;
+    CK(L.prolong<T>(v.nx, v.ny, v.nz, c.nx, c.ny, c.x, v.x));
+    for (int s = 0; s < h->prm.mg_post; ++s) {
+        CK(L.smooth<T>(A, v.b, v.x, v.xt, om, 0));
+        std::swap(v.x, v.xt);
+    }
+    return RHI_OK;
+}
+
+// z = M^-1 r, and r.z into the partials; returns the partial count
+int precond_apply(rhi_ctx* h, const double* r, double** zout, int& nparts) {
+    LinLaunch L(h->st, &h->prof);
+    const long long N = h->N;
+    if (h->prm.precond == RHI_PRECOND_JACOBI) {
+        CK(L.jacobi_dot(N, r, h->op0.diag, h->z, h->partials, nparts));
+        *zout = h->z;
+    } else if (h->prm.precond == RHI_PRECOND_MG_FP64) {
+        auto& lv = h->mg64;
+        lv[0].b = const_cast<double*>(r);
+        lv[0].x = h->z;
+        int rc = vcycle<double>(h, lv, 0, h->op0);
+        if (rc) return rc;
+        // the result may sit in either level-0 buffer
+        double* R = lv[0].x;
+        if (R != h->z) { lv[0].xt = h->z; h->z = R; }
+        *zout = h->z;
+        lv[0].x = nullptr;
+        CK(L.dot(N, r, h->z, h->partials, nparts));
+    } else {
+        auto& lv = h->mg32;
+        CK(L.to_f32(N, r, lv[0].b));
+        Op<float> A0 = level_op(h, lv[0]);
+        int rc = vcycle<float>(h, lv, 0, A0);
+        if (rc) return rc;
+        CK(L.from_f32_dot(N, lv[0].x, r, h->z, h->partials, nparts));
+        *zout = h->z;
+    }
+    h->stats.vcycles += 1;
+    return RHI_OK;
+}
+
+// CG on S sE = rhs to ||r||_RMS <= tol; solution in h->x
+int pcg(rhi_ctx* h, const double* rhs, double tol, int* its_out) {
+    LinLaunch L(h->st, &h->prof);
+    const long long N = h->N;
+    const double norm = 1.0 / ((double)N * h->nv);
+    int np = 0;
+    CK(L.cg_init(N, rhs, h->r, h->x, h->partials, np));
+    CK(L.reduce(h->partials, np, h->scal, RED_SUM, S_RR));
+    double rr;
+    int rc = read_scalar(h, S_RR, &rr);
+    if (rc) return rc;
+    int its = 0;
+    if (std::sqrt(rr * norm) > tol) {
+        double* z = nullptr;
+        if ((rc = precond_apply(h, h->r, &z, np))) return rc;
+        CK(L.reduce(h->partials, np, h->scal, RED_SUM, S_RZ));
+        CK(L.cg_p(N, h->scal, z, h->p, 1));
+        for (its = 1; its <= h->prm.max_pcg; ++its) {
+            CK(L.matvec_dot(h->op0, h->p, h->q, h->partials, np));
+            CK(L.reduce(h->partials, np, h->scal, RED_ALPHA, 0));
+            CK(L.cg_xr(N, h->scal, h->x, h->r, h->p, h->q, h->partials, np));
+            CK(L.reduce(h->partials, np, h->scal, RED_SUM, S_RR));
+            if ((rc = read_scalar(h, S_RR, &rr))) return rc;
+            if (h->h_scal[S_BREAK] != 0.0 || !std::isfinite(rr))
+                return fail(h, RHI_ERR_NONPHYSICAL, "CG breakdown: p.Sp <= 0 or non-finite residual");
+            if (std::sqrt(rr * norm) <= tol) break;
+            if ((rc = precond_apply(h, h->r, &z, np))) return rc;
+            CK(L.reduce(h->partials, np, h->scal, RED_BETA, 0));
+            CK(L.cg_p(N, h->scal, z, h->p, 0));
+        }
+        if (its > h->prm.max_pcg) its = h->prm.max_pcg;
+    }
+    *its_out = its;
+    return RHI_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// the physics launches, bracketed for the profiler
+
+PhysBuffers state_buffers(rhi_ctx* h) {
+    PhysBuffers B{};
+    B.E_n = h->E_s; B.n_n = h->n_s; B.eh = h->e_s; B.nH = h->nH; B.src = h->src; B.Tiso = h->Tiso;
+    B.g = h->g;
+    B.partials = h->partials;
+    return B;
+}
+
+int cell(rhi_ctx* h, const StepParams& P, int mode, PhysBuffers B) {
+    const int nb = (int)((h->N + cell_block_size() - 1) / cell_block_size());
+    Scope s(h->prof, mode == MODE_ITER ? "cell_residual_schur" :
+                     (mode == MODE_PREP ? "cell_prep_residual_schur" : "cell_prep_predictor"));
+    CK(launch_cell(P, h->ns, mode, B, nb, h->st));
+    return RHI_OK;
+}
+int ncell_blocks(const rhi_ctx* h) { return (int)((h->N + cell_block_size() - 1) / cell_block_size()); }
+
+int faces(rhi_ctx* h, const StepParams& P, const double* E, const double* kap, double* W) {
+    Scope s(h->prof, "faces_limiter");
+    CK(launch_faces(P, E, kap, W, h->st));
+    return RHI_OK;
+}
+int kappa(rhi_ctx* h, const StepParams& P, const double* n, double* kap) {
+    Scope s(h->prof, "kappa");
+    CK(launch_kappa(P, h->ns, n, kap, h->st));
+    return RHI_OK;
+}
+
+void set_op0(rhi_ctx* h, const StepParams& P, int set, const double* W) {
+    Op<double>& A = h->op0;
+    A.nx = h->grid.nx; A.ny = h->grid.ny; A.nz = h->grid.nz; A.N = h->N;
+    for (int a = 0; a < 3; ++a) { A.per[a] = h->per[a]; A.W[a] = W + a * h->N; }
+    A.diag = h->diag[set];
+    A.scale = P.dth;
+}
+
+// U views of a work buffer
+double* U_ec(rhi_ctx* h, int b) { return h->U[b]; }
+double* U_n(rhi_ctx* h, int b) { return h->U[b] + h->N; }
+double* U_E(rhi_ctx* h, int b) { return h->U[b] + (long long)(1 + h->ns) * h->N; }
+
+int validate_params(const rhi_params* p) {
+    if (p->n_species != 1 && p->n_species != 3) return 0;
+    if (p->n_species == 1 && p->y_he != 0.0) return 0;
+    if (!(p->y_he >= 0.0)) return 0;
+    if (!(p->theta > 0.0 && p->theta <= 1.0)) return 0;
+    if (!(p->u_e > 0.0 && p->u_n > 0.0 && p->u_E > 0.0)) return 0;
+    if (!(p->tau > 0.0 && p->tau < 1.0)) return 0;
+    if (!(p->lam_min > 0.0 && p->lam_min <= 1.0)) return 0;
+    if (p->max_newton < 0 || p->max_pcg < 1) return 0;
+    if (p->guess < 0 || p->guess > RHI_GUESS_PREDICTOR) return 0;
+    if (p->precond < 0 || p->precond > RHI_PRECOND_MG_FP32) return 0;
+    if (p->mg_levels < 1 || p->mg_pre < 1 || p->mg_post < 0 || p->mg_coarse_sweeps < 1) return 0;
+    if (!(p->mg_omega > 0.0 && p->mg_omega <= 1.0)) return 0;
+    return 1;
+}
+
+}  // namespace
+
+// =============================================================================================
+// C ABI
+
+extern "C" {
+
+int rhi_params_default(rhi_params* p, int n_species) {
+    if (!p || (n_species != 1 && n_species != 3)) return RHI_ERR_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->n_species = n_species;
+    p->y_he = 0.0;
+    p->theta = 0.51;
+    p->m_grey = 1;
+    p->isothermal = 0;
+    p->limiter = 1;
+    p->kappa_floor = 1e-40;
+    p->u_e = p->u_n = p->u_E = 1.0;
+    p->tau = 0.99;
+    p->lam_min = 1.0 / 16.0;
+    p->max_newton = 50;
+    p->max_pcg = 200;
+    p->guess = RHI_GUESS_PREVIOUS;
+    p->precond = RHI_PRECOND_MG_FP64;
+    p->mg_levels = 6;
+    p->mg_pre = 2;
+    p->mg_post = 2;
+    p->mg_coarse_sweeps = 16;
+    p->mg_omega = 0.8;
+    return rhi_grey_constants(RHI_SPECTRUM_MONO, 13.6 * EV, n_species, p->sk, p->pgam, p->ph,
+                              &p->photon_energy);
+}
+
+int rhi_create(const rhi_grid* grid, const rhi_bc* bc, const rhi_params* params, void* stream,
+               rhi_handle* out) {
+    if (!grid || !bc || !params || !out) return RHI_ERR_ARG;
+    *out = nullptr;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->dx > 0.0)) return RHI_ERR_ARG;
+    const long long N = (long long)grid->nx * grid->ny * grid->nz;
+    if (N > (1LL << 31)) return RHI_ERR_ARG;
+    for (int a = 0; a < 3; ++a) {
+        const int lo = bc->kind[2 * a], hi = bc->kind[2 * a + 1];
+        if ((lo != RHI_BC_ZERO_FLUX && lo != RHI_BC_PERIODIC) ||
+            (hi != RHI_BC_ZERO_FLUX && hi != RHI_BC_PERIODIC) || (lo == RHI_BC_PERIODIC) != (hi == RHI_BC_PERIODIC))
+            return RHI_ERR_ARG;
+    }
+    if (!validate_params(params)) return RHI_ERR_ARG;
+
+    rhi_ctx* h = new rhi_ctx();
+    h->grid = *grid;
+    h->bc = *bc;
+    h->prm = *params;
+    h->ns = params->n_species;
+    h->nv = h->ns + 2;
+    h->nm = h->ns + 1;
+    h->N = N;
+    for (int a = 0; a < 3; ++a) h->per[a] = bc->kind[2 * a] == RHI_BC_PERIODIC;
+    h->st = (cudaStream_t)stream;
+    h->prof.st = h->st;
+
+    int rc = RHI_OK;
+    auto A = [&](double** p, size_t n) { if (!rc) rc = dalloc(h, p, n); };
+    A(&h->E_s, N); A(&h->e_s, N); A(&h->n_s, (size_t)h->ns * N); A(&h->nH, N); A(&h->src, N);
+    A(&h->Tiso, N);
+    for (int b = 0; b < 2; ++b) {
+        A(&h->U[b], (size_t)h->nv * N); A(&h->kap[b], N); A(&h->W[b], 3 * (size_t)N);
+        A(&h->diag[b], N); A(&h->rhs[b], N); A(&h->fMt[b], (size_t)h->nm * N);
+        A(&h->MiU[b], (size_t)h->nm * N);
+    }
+    A(&h->g, (size_t)h->nv * N);
+    A(&h->x, N); A(&h->r, N); A(&h->z, N); A(&h->p, N); A(&h->q, N);
+    const long long nparts = std::max<long long>((N + cell_block_size() - 1) / cell_block_size(),
+                                                 stream_blocks(N));
+    A(&h->partials, (size_t)nparts);
+    A(&h->scal, S_NSCAL);
+    if (!rc) rc = dalloc(h, &h->d_flag, 1);
+    if (!rc) rc = dalloc(h, &h->table, (size_t)NBINS * NRATES);
+    if (!rc) rc = mg_build_levels(h);
+    if (!rc) {
+        cudaError_t e = cudaMallocHost(&h->h_scal, sizeof(double) * S_NSCAL);
+        if (e != cudaSuccess) rc = fail(h, RHI_ERR_CUDA, "cudaMallocHost");
+    }
+    if (!rc) {
+        std::vector<double2> tab = build_rate_table();
+        cudaError_t e = cudaMemcpy(h->table, tab.data(), tab.size() * sizeof(double2), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(h->src, 0, N * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemset(h->scal, 0, S_NSCAL * sizeof(double));
+        if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
+        if (e != cudaSuccess) rc = fail(h, RHI_ERR_CUDA, std::string("rhi_create: ") + cudaGetErrorString(e));
+    }
+    if (rc) {
+        rhi_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return RHI_OK;
+}
+
+void rhi_destroy(rhi_handle h) {
+    if (!h) return;
+    if (h->st) cudaStreamSynchronize(h->st);
+    else cudaDeviceSynchronize();
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->h_scal) cudaFreeHost(h->h_scal);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    delete h;
+}
+
+const char* rhi_last_error(rhi_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+const char* rhi_status_string(int s) {
+    switch (s) {
+        case RHI_OK: return "ok";
+        case RHI_ERR_ARG: return "invalid argument";
+        case RHI_ERR_CUDA: return "CUDA error";
+        case RHI_ERR_NONCONVERGED: return "Newton iteration did not converge";
+        case RHI_ERR_NONPHYSICAL: return "non-physical state or CG breakdown";
+        case RHI_ERR_STATE: return "no state set";
+        default: return "unknown status";
+    }
+}
+
+int rhi_set_state(rhi_handle h, const double* E, const double* e, const double* n,
+                  const double* n_H, const double* src, int on_device) {
+    if (!h) return RHI_ERR_ARG;
+    if (!E || !e || !n || !n_H) return fail(h, RHI_ERR_ARG, "rhi_set_state: null field");
+    const long long N = h->N;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(h->E_s, E, N * sizeof(double), kind, h->st));
+    CK(cudaMemcpyAsync(h->e_s, e, N * sizeof(double), kind, h->st));
+    CK(cudaMemcpyAsync(h->n_s, n, (size_t)h->ns * N * sizeof(double), kind, h->st));
+    CK(cudaMemcpyAsync(h->nH, n_H, N * sizeof(double), kind, h->st));
+    if (src) CK(cudaMemcpyAsync(h->src, src, N * sizeof(double), kind, h->st));
+    else CK(cudaMemsetAsync(h->src, 0, N * sizeof(double), h->st));
+    StepParams P = make_params(h, 1.0, 1.0, 0.0);
+    CK(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->st));
+    {
+        Scope s(h->prof, "check_state");
+        CK(launch_check_state(P, h->ns, h->E_s, h->e_s, h->n_s, h->nH, h->d_flag, h->st));
+    }
+    if (h->prm.isothermal) {
+        Scope s(h->prof, "temperature");
+        CK(launch_temperature(P, h->ns, h->e_s, h->n_s, h->nH, h->Tiso, h->st));
+    }
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->prof.resolve();
+    h->have_linear = false;
+    if (bad) {
+        h->have_state = false;
+        return fail(h, RHI_ERR_NONPHYSICAL, "rhi_set_state: need E > 0, e > 0, n_H > 0, species >= 0, finite");
+    }
+    h->have_state = true;
+    return RHI_OK;
+}
+
+int rhi_set_sources(rhi_handle h, int nsrc, const int* ijk, const double* rate) {
+    if (!h) return RHI_ERR_ARG;
+    if (nsrc < 0 || (nsrc > 0 && (!ijk || !rate))) return fail(h, RHI_ERR_ARG, "rhi_set_sources: bad arguments");
+    const double vol = h->grid.dx * h->grid.dx * h->grid.dx;
+    for (int s = 0; s < nsrc; ++s) {
+        const int i = ijk[3 * s], j = ijk[3 * s + 1], k = ijk[3 * s + 2];
+        if (i < 0 || j < 0 || k < 0 || i >= h->grid.nx || j >= h->grid.ny || k >= h->grid.nz)
+            return fail(h, RHI_ERR_ARG, "rhi_set_sources: source outside the grid");
+        if (!(rate[s] >= 0.0)) return fail(h, RHI_ERR_ARG, "rhi_set_sources: negative rate");
+    }
+    for (int s = 0; s < nsrc; ++s) {
+        const long long c = ijk[3 * s] + (long long)h->grid.nx * (ijk[3 * s + 1] + (long long)h->grid.ny * ijk[3 * s + 2]);
+        Scope sc(h->prof, "deposit_source");
+        CK(launch_deposit(c, rate[s] * h->prm.photon_energy / vol, h->src, h->st));
+    }
+    CK(cudaStreamSynchronize(h->st));
+    h->prof.resolve();
+    return RHI_OK;
+}
+
+int rhi_get_state(rhi_handle h, double* E, double* e, double* n, int on_device) {
+    if (!h) return RHI_ERR_ARG;
+    if (!h->have_state) return fail(h, RHI_ERR_STATE, "rhi_get_state: no state");
+    const long long N = h->N;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (E) CK(cudaMemcpyAsync(E, h->E_s, N * sizeof(double), kind, h->st));
+    if (e) CK(cudaMemcpyAsync(e, h->e_s, N * sizeof(double), kind, h->st));
+    if (n) CK(cudaMemcpyAsync(n, h->n_s, (size_t)h->ns * N * sizeof(double), kind, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return RHI_OK;
+}
+
+int rhi_get_stats(rhi_handle h, rhi_stats* out) {
+    if (!h || !out) return RHI_ERR_ARG;
+    *out = h->stats;
+    return RHI_OK;
+}
+
+int rhi_set_profiling(rhi_handle h, int on) {
+    if (!h) return RHI_ERR_ARG;
+    h->prof.on = on != 0;
+    h->prof.acc.clear();
+    return RHI_OK;
+}
+
+int rhi_kernel_times(rhi_handle h, int max, char* names, double* total_ms, int* launches) {
+    if (!h) return -RHI_ERR_ARG;
+    h->prof.resolve();
+    int i = 0;
+    for (auto& kv : h->prof.acc) {
+        if (i < max) {
+            if (names) {
+                std::strncpy(names + 48 * i, kv.first.c_str(), 47);
+                names[48 * i + 47] = 0;
+            }
+            if (total_ms) total_ms[i] = kv.second.first;
+            if (launches) launches[i] = kv.second.second;
+        }
+        ++i;
+    }
+    return i;
+}
+
+int rhi_linearize(rhi_handle h, double dt, double a, double adot, double* f, double* S_diag,
+                  double* S_face, double* rhs, int on_device) {
+    if (!h) return RHI_ERR_ARG;
+    if (!h->have_state) return fail(h, RHI_ERR_STATE, "rhi_linearize: no state");
+    if (!(dt > 0.0) || !(a > 0.0)) return fail(h, RHI_ERR_ARG, "rhi_linearize: dt > 0 and a > 0 required");
+    const StepParams P = make_params(h, dt, a, adot);
+    int rc;
+    if ((rc = kappa(h, P, h->n_s, h->kap[0]))) return rc;
+    if ((rc = faces(h, P, h->E_s, h->kap[0], h->W[0]))) return rc;
+    PhysBuffers B = state_buffers(h);
+    B.W = h->W[0];
+    B.diag = h->diag[0]; B.rhs = h->rhs[0]; B.fMt = h->fMt[0]; B.MiU = h->MiU[0];
+    // residual: straight into a device destination, or via a free work buffer for the host
+    if (f) B.f_out = on_device ? f : h->U[1];
+    if ((rc = cell(h, P, MODE_PREP, B))) return rc;
+    set_op0(h, P, 0, h->W[0]);
+    if ((rc = precond_setup(h))) return rc;
+    const long long N = h->N;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (f && !on_device) CK(cudaMemcpyAsync(f, h->U[1], (size_t)h->nv * N * sizeof(double), kind, h->st));
+    if (S_diag) CK(cudaMemcpyAsync(S_diag, h->diag[0], N * sizeof(double), kind, h->st));
+    if (rhs) CK(cudaMemcpyAsync(rhs, h->rhs[0], N * sizeof(double), kind, h->st));
+    if (S_face) {
+        // S_face = dt theta W (scaled on the host; a test and inspection path)
+        std::vector<double> tmp(3 * (size_t)N);
+        CK(cudaMemcpyAsync(tmp.data(), h->W[0], 3 * N * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        CK(cudaStreamSynchronize(h->st));
+        for (auto& v : tmp) v *= P.dth;
+        if (on_device) CK(cudaMemcpy(S_face, tmp.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice));
+        else std::memcpy(S_face, tmp.data(), 3 * N * sizeof(double));
+    }
+    CK(cudaStreamSynchronize(h->st));
+    h->prof.resolve();
+    h->have_linear = true;
+    return RHI_OK;
+}
+
+int rhi_precond_apply(rhi_handle h, const double* r, double* z, int on_device) {
+    if (!h || !r || !z) return RHI_ERR_ARG;
+    if (!h->have_linear) return fail(h, RHI_ERR_STATE, "rhi_precond_apply: call rhi_linearize first");
+    const long long N = h->N;
+    CK(cudaMemcpyAsync(h->q, r, N * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+    double* zr = nullptr;
+    int np = 0;
+    int rc = precond_apply(h, h->q, &zr, np);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(z, zr, N * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->prof.resolve();
+    return RHI_OK;
+}
+
+int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double newton_tol,
+                      double lin_tol) {
+    if (!h) return RHI_ERR_ARG;
+    if (!h->have_state) return fail(h, RHI_ERR_STATE, "rhi_implicit_step: no state");
+    if (!(dt > 0.0) || !(a > 0.0) || !(newton_tol > 0.0) || !(lin_tol > 0.0) || !std::isfinite(adot))
+        return fail(h, RHI_ERR_ARG, "rhi_implicit_step: need dt > 0, a > 0, tolerances > 0");
+    h->have_linear = false;
+    rhi_stats& S = h->stats;
+    S = rhi_stats{};
+    S.status = RHI_OK;
+    const int launches0 = h->prof.launches;
+    const StepParams P = make_params(h, dt, a, adot);
+    const long long N = h->N;
+    const int ns = h->ns;
+    LinLaunch L(h->st, &h->prof);
+    CK(cudaEventRecord(h->ev0, h->st));
+    int rc;
+
+    // ---- g^n and the initial iterate U_0
+    if ((rc = kappa(h, P, h->n_s, h->kap[0]))) return rc;
+    if ((rc = faces(h, P, h->E_s, h->kap[0], h->W[0]))) return rc;
+    PhysBuffers B = state_buffers(h);
+    B.W = h->W[0];
+    int cur = -1;            // -1: U_k is the state U^n (e_c = 0); 0 / 1: work buffer
+    int set = 0;             // Schur set of U_k
+    double res = 0.0;
+    if (h->prm.guess == RHI_GUESS_PREVIOUS) {
+        B.diag = h->diag[0]; B.rhs = h->rhs[0]; B.fMt = h->fMt[0]; B.MiU = h->MiU[0];
+        if ((rc = cell(h, P, MODE_PREP, B))) return rc;
+        if ((rc = residual_norm(h, ncell_blocks(h), &res))) return rc;
+    } else {
+        B.U0 = h->U[0];
+        if ((rc = cell(h, P, MODE_PREP_PREDICT, B))) return rc;
+        cur = 0;
+        if ((rc = kappa(h, P, U_n(h, 0), h->kap[0]))) return rc;
+        if ((rc = faces(h, P, U_E(h, 0), h->kap[0], h->W[0]))) return rc;
+        PhysBuffers C = state_buffers(h);
+        C.ec = U_ec(h, 0); C.n = U_n(h, 0); C.E = U_E(h, 0); C.W = h->W[0];
+        C.diag = h->diag[0]; C.rhs = h->rhs[0]; C.fMt = h->fMt[0]; C.MiU = h->MiU[0];
+        if ((rc = cell(h, P, MODE_ITER, C))) return rc;
+        if ((rc = residual_norm(h, ncell_blocks(h), &res))) return rc;
+    }
+    S.guess_used = h->prm.guess;
+    S.res_initial = res;
+    if (!std::isfinite(res)) { S.status = RHI_ERR_NONPHYSICAL; return fail(h, RHI_ERR_NONPHYSICAL, "non-finite initial residual"); }
+
+    // ---- Newton iteration
+    int k = 0;
+    while (!(res < newton_tol) && k < h->prm.max_newton) {
+        const double* Wk = h->W[cur < 0 ? 0 : cur];
+        set_op0(h, P, set, Wk);
+        if ((rc = precond_setup(h))) return rc;
+        int its = 0;
+        if ((rc = pcg(h, h->rhs[set], lin_tol * res, &its))) { S.status = rc; return rc; }
+        S.pcg_its += its;
+        const int t = (cur == 0) ? 1 : 0;
+        const double* ec0 = cur < 0 ? nullptr : U_ec(h, cur);
+        const double* n0 = cur < 0 ? h->n_s : U_n(h, cur);
+        const double* E0 = cur < 0 ? h->E_s : U_E(h, cur);
+        double lam = 1.0, rt = 0.0;
+        bool fallback = false;
+        while (true) {
+            {
+                Scope s(h->prof, "update_recover_limit");
+                CK(launch_update(P, ns, lam, ec0, n0, E0, h->e_s, h->nH, h->x, h->fMt[set],
+                                 h->MiU[set], U_ec(h, t), U_n(h, t), U_E(h, t), h->kap[t], h->st));
+            }
+            if ((rc = faces(h, P, U_E(h, t), h->kap[t], h->W[t]))) return rc;
+            PhysBuffers C = state_buffers(h);
+            C.ec = U_ec(h, t); C.n = U_n(h, t); C.E = U_E(h, t); C.W = h->W[t];
+            C.diag = h->diag[1 - set]; C.rhs = h->rhs[1 - set];
+            C.fMt = h->fMt[1 - set]; C.MiU = h->MiU[1 - set];
+            if ((rc = cell(h, P, MODE_ITER, C))) return rc;
+            if ((rc = residual_norm(h, ncell_blocks(h), &rt))) return rc;
+            if (fallback || rt <= (1.0 - 1e-4 * lam) * res) break;
+            if (lam * 0.5 < h->prm.lam_min) { lam = 1.0; fallback = true; S.full_steps += 1; continue; }
+            lam *= 0.5;
+            S.backtracks += 1;
+        }
+        cur = t;
+        set = 1 - set;
+        res = rt;
+        ++k;
+        if (!std::isfinite(res)) break;
+    }
+    S.newton_its = k;
+    S.res_final = res;
+    if (!std::isfinite(res)) {
+        S.status = RHI_ERR_NONPHYSICAL;
+        S.launches = h->prof.launches - launches0;
+        h->prof.resolve();
+        return fail(h, RHI_ERR_NONPHYSICAL, "non-finite residual during Newton");
+    }
+    if (!(res < newton_tol)) {
+        S.status = RHI_ERR_NONCONVERGED;
+        S.launches = h->prof.launches - launches0;
+        h->prof.resolve();
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "Newton: ||f|| = %.3e >= %.3e after %d iterations", res, newton_tol, k);
+        return fail(h, RHI_ERR_NONCONVERGED, buf);
+    }
+    // ---- accept: U^{n+1} -> state, e^{n+1} = e_h + e_c
+    if (cur >= 0) {
+        {
+            Scope s(h->prof, "finalize_energy");
+            CK(launch_finalize(P, ns, U_ec(h, cur), h->e_s, h->st));
+        }
+        CK(cudaMemcpyAsync(h->n_s, U_n(h, cur), (size_t)ns * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        CK(cudaMemcpyAsync(h->E_s, U_E(h, cur), N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    }
+    CK(cudaEventRecord(h->ev1, h->st));
+    CK(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    S.ms = ms;
+    S.launches = h->prof.launches - launches0;
+    h->prof.resolve();
+    return RHI_OK;
+}
+
+}  // extern "C"

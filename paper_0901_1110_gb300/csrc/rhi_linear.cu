@@ -1,0 +1,495 @@
+// Scalar Schur-system solve (Sec. 3.2.1, step (ii)): conjugate gradients on the 7-point
+// matrix S, preconditioned by one geometric multigrid V-cycle (FP64, or FP32 for the mixed-
+// precision form) or by Jacobi.  Reductions are deterministic: per-block partial sums are
+// added in a fixed order by a single block.
+//
+// Operator of a level: (A x)_c = diag_c x_c - scale * sum_faces W_f x_nb(f), where W holds the
+// coefficient of each cell's lower face per axis (0 on zero-flux boundary faces).
+#include "rhi_linear.cuh"
+
+namespace rhi {
+
+constexpr int LIN_BLOCK = 256;
+
+int stream_blocks(long long N) {
+    const long long want = (N + LIN_BLOCK - 1) / LIN_BLOCK;
+    const long long cap = 152LL * 16;                 // 16 resident blocks per SM x 152 SMs
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+template <typename T>
+__device__ __forceinline__ void coords3(const Op<T>& A, long long c, int& i, int& j, int& k) {
+    const long long nxy = (long long)A.nx * A.ny;
+    k = (int)(c / nxy);
+    const long long r = c - (long long)k * nxy;
+    j = (int)(r / A.nx);
+    i = (int)(r - (long long)j * A.nx);
+}
+
+// (A x)_c with the six neighbours of c
+template <typename T, typename TX>
+__device__ __forceinline__ T apply_row(const Op<T>& A, const TX* __restrict__ x, long long c,
+                                       int i, int j, int k, T xc) {
+    const long long sx = 1, sy = A.nx, sz = (long long)A.nx * A.ny;
+    const int n[3] = {A.nx, A.ny, A.nz};
+    const int q[3] = {i, j, k};
+    const long long s[3] = {sx, sy, sz};
+    const int per[3] = {A.per[0], A.per[1], A.per[2]};
+    T off = T(0);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        long long lo, hi;
+        bool has_hi = true;
+        if (q[ax] > 0) lo = c - s[ax];
+        else lo = c + (long long)(n[ax] - 1) * s[ax];            // W = 0 there unless periodic
+        if (q[ax] < n[ax] - 1) hi = c + s[ax];
+        else if (per[ax]) hi = c - (long long)(n[ax] - 1) * s[ax];
+        else { hi = c; has_hi = false; }
+        const T wlo = A.W[ax][c];
+        off += wlo * T(x[lo]);
+        if (has_hi) off += A.W[ax][hi] * T(x[hi]);
+    }
+    return A.diag[c] * xc - A.scale * off;
+}
+
+// ---------------------------------------------------------------------------------------------
+// CG building blocks (FP64)
+
+__global__ void __launch_bounds__(LIN_BLOCK) k_matvec_dot(const Op<double> A,
+                                                          const double* __restrict__ p,
+                                                          double* __restrict__ q,
+                                                          double* __restrict__ partials) {
+    double acc = 0.0;
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < A.N;
+         c += (long long)gridDim.x * LIN_BLOCK) {
+        int i, j, k;
+        coords3(A, c, i, j, k);
+        const double pc = p[c];
+        const double v = apply_row(A, p, c, i, j, k, pc);
+        q[c] = v;
+        acc += pc * v;
+    }
+    const double s = block_sum<LIN_BLOCK>(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// x += alpha p; r -= alpha q; partial r.r      (alpha = scal[S_ALPHA])
+__global__ void __launch_bounds__(LIN_BLOCK) k_cg_xr(long long N, const double* __restrict__ scal,
+                                                     double* __restrict__ x, double* __restrict__ r,
+                                                     const double* __restrict__ p,
+                                                     const double* __restrict__ q,
+                                                     double* __restrict__ partials) {
+    const double alpha = scal[S_ALPHA];
+    double acc = 0.0;
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+         c += (long long)gridDim.x * LIN_BLOCK) {
+        x[c] += alpha * p[c];
+        const double rv = r[c] - alpha * q[c];
+        r[c] = rv;
+        acc += rv * rv;
+    }
+    const double s = block_sum<LIN_BLOCK>(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// p = z + beta p    (beta = scal[S_BETA]); first: p = z
+__global__ void __launch_bounds__(LIN_BLOCK) k_cg_p(long long N, const double* __restrict__ scal,
+                                                    const double* __restrict__ z,
+                                                    double* __restrict__ p, int first) {
+    const double beta = first ? 0.0 : scal[S_BETA];
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+         c += (long long)gridDim.x * LIN_BLOCK)
+        p[c] = first ? z[c] : z[c] + beta * p[c];
+}
+
+// z = r / diag; partial r.z
+__global__ void __launch_bounds__(LIN_BLOCK) k_jacobi_dot(long long N, const double* __restrict__ r,
+                                                          const double* __restrict__ diag,
+                                                          double* __restrict__ z,
+                                                          double* __restrict__ partials) {
+    double acc = 0.0;
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+         c += (long long)gridDim.x * LIN_BLOCK) {
+        const double rv = r[c];
+        const double zv = rv / diag[c];
+        z[c] = zv;
+        acc += rv * zv;
+    }
+    const double s = block_sum<LIN_BLOCK>(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// partial a.b
+__global__ void __launch_bounds__(LIN_BLOCK) k_dot(long long N, const double* __restrict__ a,
+                                                   const double* __restrict__ b,
+                                                   double* __restrict__ partials) {
+    double acc = 0.0;
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+         c += (long long)gridDim.x * LIN_BLOCK)
+        acc += a[c] * b[c];
+    const double s = block_sum<LIN_BLOCK>(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// r = b, x = 0; partial r.r
+__global__ void __launch_bounds__(LIN_BLOCK) k_cg_init(long long N, const double* __restrict__ b,
+                                                       double* __restrict__ r,
+                                                       double* __restrict__ x,
+                                                       double* __restrict__ partials) {
+    double acc = 0.0;
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+         c += (long long)gridDim.x * LIN_BLOCK) {
+        const double v = b[c];
+        r[c] = v;
+        x[c] = 0.0;
+        acc += v * v;
+    }
+    const double s = block_sum<LIN_BLOCK>(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// Sum of partials in a fixed order, then a scalar update:
+//   SUM_TO(k):   scal[k] = sum
+//   SUM_ALPHA:   scal[S_PQ] = sum; scal[S_ALPHA] = scal[S_RZ] / sum (breakdown flag if <= 0)
+//   SUM_BETA:    scal[S_BETA] = sum / scal[S_RZ]; scal[S_RZ] = sum
+constexpr int RED_BLOCK = 1024;
+__global__ void __launch_bounds__(RED_BLOCK) k_reduce(const double* __restrict__ partials, int n,
+                                                      double* __restrict__ scal, int op,
+                                                      int slot) {
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < n; q += RED_BLOCK) acc += partials[q];
+    const double s = block_sum<RED_BLOCK>(acc);
+    if (threadIdx.x == 0) {
+        if (op == RED_SUM) {
+            scal[slot] = s;
+        } else if (op == RED_ALPHA) {
+            scal[S_PQ] = s;
+            if (!(s > 0.0)) scal[S_BREAK] = 1.0;
+            scal[S_ALPHA] = (s > 0.0) ? scal[S_RZ] / s : 0.0;
+        } else {
+            scal[S_BETA] = s / scal[S_RZ];
+            scal[S_RZ] = s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// multigrid kernels (templated on the level precision)
+
+// weighted Jacobi: first sweep from x = 0: x_out = omega b / diag; else
+// x_out = x_in + omega (b - A x_in) / diag
+template <typename T>
+__global__ void __launch_bounds__(LIN_BLOCK) k_mg_smooth(const Op<T> A, const T* __restrict__ b,
+                                                         const T* __restrict__ xin,
+                                                         T* __restrict__ xout, T omega,
+                                                         int first) {
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < A.N;
+         c += (long long)gridDim.x * LIN_BLOCK) {
+        const T d = A.diag[c];
+        if (first) {
+            xout[c] = omega * b[c] / d;
+        } else {
+            int i, j, k;
+            coords3(A, c, i, j, k);
+            const T xc = xin[c];
+            const T ax = apply_row(A, xin, c, i, j, k, xc);
+            xout[c] = xc + omega * (b[c] - ax) / d;
+        }
+    }
+}
+
+// coarse right-hand side: mean over the existing children of the fine residual b - A x
+template <typename T>
+__global__ void __launch_bounds__(LIN_BLOCK) k_mg_restrict(const Op<T> A, const T* __restrict__ b,
+                                                           const T* __restrict__ x, int cnx,
+                                                           int cny, int cnz,
+                                                           T* __restrict__ bc) {
+    const long long Nc = (long long)cnx * cny * cnz;
+    for (long long cc = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; cc < Nc;
+         cc += (long long)gridDim.x * LIN_BLOCK) {
+        const int K = (int)(cc / ((long long)cnx * cny));
+        const long long rem = cc - (long long)K * cnx * cny;
+        const int J = (int)(rem / cnx), I = (int)(rem - (long long)J * cnx);
+        T acc = T(0);
+        int cnt = 0;
+        for (int dk = 0; dk < 2; ++dk) {
+            const int k = 2 * K + dk;
+            if (k >= A.nz) continue;
+            for (int dj = 0; dj < 2; ++dj) {
+                const int j = 2 * J + dj;
+                if (j >= A.ny) continue;
+                for (int di = 0; di < 2; ++di) {
+                    const int i = 2 * I + di;
+                    if (i >= A.nx) continue;
+                    const long long c = i + (long long)A.nx * (j + (long long)A.ny * k);
+                    acc += b[c] - apply_row(A, x, c, i, j, k, x[c]);
+                    ++cnt;
+                }
+            }
+        }
+        bc[cc] = acc / T(cnt);
+    }
+}
+
+// x_f += x_c(parent)
+template <typename T>
+__global__ void __launch_bounds__(LIN_BLOCK) k_mg_prolong(int nx, int ny, int nz, int cnx, int cny,
+                                                          const T* __restrict__ xc,
+                                                          T* __restrict__ xf) {
+    const long long N = (long long)nx * ny * nz;
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+         c += (long long)gridDim.x * LIN_BLOCK) {
+        const int k = (int)(c / ((long long)nx * ny));
+        const long long rem = c - (long long)k * nx * ny;
+        const int j = (int)(rem / nx), i = (int)(rem - (long long)j * nx);
+        xf[c] += xc[(i >> 1) + (long long)cnx * ((j >> 1) + (long long)cny * (k >> 1))];
+    }
+}
+
+// Coarse operator by re-discretisation: local diagonal = mean of the children's local
+// diagonals (diag - scale * sum of their six faces); lower-face coefficient of the coarse
+// cell = (mean of the existing fine lower faces of its first-layer children) / 4.
+// Writes diag_c = local part only; k_mg_diag_faces adds the face sums.
+template <typename TF, typename TC>
+__global__ void __launch_bounds__(LIN_BLOCK) k_mg_coarsen(const Op<TF> A, int cnx, int cny,
+                                                          int cnz, TC* __restrict__ dc,
+                                                          TC* __restrict__ wcx,
+                                                          TC* __restrict__ wcy,
+                                                          TC* __restrict__ wcz) {
+    const long long Nc = (long long)cnx * cny * cnz;
+    const long long sz = (long long)A.nx * A.ny;
+    for (long long cc = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; cc < Nc;
+         cc += (long long)gridDim.x * LIN_BLOCK) {
+        const int K = (int)(cc / ((long long)cnx * cny));
+        const long long rem = cc - (long long)K * cnx * cny;
+        const int J = (int)(rem / cnx), I = (int)(rem - (long long)J * cnx);
+        double dl = 0.0, wx = 0.0, wy = 0.0, wz = 0.0;
+        int cnt = 0, nxf = 0, nyf = 0, nzf = 0;
+        for (int dk = 0; dk < 2; ++dk) {
+            const int k = 2 * K + dk;
+            if (k >= A.nz) continue;
+            for (int dj = 0; dj < 2; ++dj) {
+                const int j = 2 * J + dj;
+                if (j >= A.ny) continue;
+                for (int di = 0; di < 2; ++di) {
+                    const int i = 2 * I + di;
+                    if (i >= A.nx) continue;
+                    const long long c = i + (long long)A.nx * (j + (long long)A.ny * k);
+                    // six face coefficients of the child
+                    double fsum = 0.0;
+                    const int q[3] = {i, j, k};
+                    const int n[3] = {A.nx, A.ny, A.nz};
+                    const long long s[3] = {1, A.nx, sz};
+#pragma unroll
+                    for (int ax = 0; ax < 3; ++ax) {
+                        fsum += (double)A.W[ax][c];
+                        if (q[ax] < n[ax] - 1) fsum += (double)A.W[ax][c + s[ax]];
+                        else if (A.per[ax]) fsum += (double)A.W[ax][c - (long long)(n[ax] - 1) * s[ax]];
+                    }
+                    dl += (double)A.diag[c] - (double)A.scale * fsum;
+                    ++cnt;
+                    if (di == 0) { wx += (double)A.W[0][c]; ++nxf; }
+                    if (dj == 0) { wy += (double)A.W[1][c]; ++nyf; }
+                    if (dk == 0) { wz += (double)A.W[2][c]; ++nzf; }
+                }
+            }
+        }
+        const double sc = (double)A.scale * 0.25;
+        dc[cc] = (TC)(dl / cnt);
+        wcx[cc] = (TC)(sc * wx / nxf);
+        wcy[cc] = (TC)(sc * wy / nyf);
+        wcz[cc] = (TC)(sc * wz / nzf);
+    }
+}
+
+// diag += sum of the six face coefficients (scale 1 on coarse levels)
+template <typename T>
+__global__ void __launch_bounds__(LIN_BLOCK) k_mg_diag_faces(Op<T> A, T* __restrict__ diag) {
+    const long long sz = (long long)A.nx * A.ny;
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < A.N;
+         c += (long long)gridDim.x * LIN_BLOCK) {
+        int i, j, k;
+        coords3(A, c, i, j, k);
+        const int q[3] = {i, j, k};
+        const int n[3] = {A.nx, A.ny, A.nz};
+        const long long s[3] = {1, A.nx, sz};
+        T f = T(0);
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            f += A.W[ax][c];
+            if (q[ax] < n[ax] - 1) f += A.W[ax][c + s[ax]];
+            else if (A.per[ax]) f += A.W[ax][c - (long long)(n[ax] - 1) * s[ax]];
+        }
+        diag[c] += f;
+    }
+}
+
+// FP32 copy of the finest operator with the scale folded into the faces
+__global__ void __launch_bounds__(LIN_BLOCK) k_cast_op(const Op<double> A, float* __restrict__ d,
+                                                       float* __restrict__ wx,
+                                                       float* __restrict__ wy,
+                                                       float* __restrict__ wz) {
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < A.N;
+         c += (long long)gridDim.x * LIN_BLOCK) {
+        d[c] = (float)A.diag[c];
+        wx[c] = (float)(A.scale * A.W[0][c]);
+        wy[c] = (float)(A.scale * A.W[1][c]);
+        wz[c] = (float)(A.scale * A.W[2][c]);
+    }
+}
+
+__global__ void __launch_bounds__(LIN_BLOCK) k_to_f32(long long N, const double* __restrict__ a,
+                                                      float* __restrict__ b) {
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+         c += (long long)gridDim.x * LIN_BLOCK)
+        b[c] = (float)a[c];
+}
+
+// z = x (widened); partial r.z
+__global__ void __launch_bounds__(LIN_BLOCK) k_from_f32_dot(long long N, const float* __restrict__ x,
+                                                            const double* __restrict__ r,
+                                                            double* __restrict__ z,
+                                                            double* __restrict__ partials) {
+    double acc = 0.0;
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+         c += (long long)gridDim.x * LIN_BLOCK) {
+        const double zv = (double)x[c];
+        z[c] = zv;
+        acc += r[c] * zv;
+    }
+    const double s = block_sum<LIN_BLOCK>(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// ---------------------------------------------------------------------------------------------
+// host-side launchers
+
+LinLaunch::LinLaunch(cudaStream_t s, LaunchHook* h) : st(s), hook(h) {}
+
+void LinLaunch::begin(const char* name) { if (hook) hook->begin(name); }
+cudaError_t LinLaunch::end() {
+    cudaError_t e = cudaGetLastError();
+    if (hook) hook->end();
+    return e;
+}
+
+cudaError_t LinLaunch::matvec_dot(const Op<double>& A, const double* p, double* q, double* part,
+                                  int& nparts) {
+    nparts = stream_blocks(A.N);
+    begin("cg_matvec_dot");
+    k_matvec_dot<<<nparts, LIN_BLOCK, 0, st>>>(A, p, q, part);
+    return end();
+}
+cudaError_t LinLaunch::cg_xr(long long N, const double* scal, double* x, double* r,
+                             const double* p, const double* q, double* part, int& nparts) {
+    nparts = stream_blocks(N);
+    begin("cg_update_xr");
+    k_cg_xr<<<nparts, LIN_BLOCK, 0, st>>>(N, scal, x, r, p, q, part);
+    return end();
+}
+cudaError_t LinLaunch::cg_p(long long N, const double* scal, const double* z, double* p, int first) {
+    begin("cg_update_p");
+    k_cg_p<<<stream_blocks(N), LIN_BLOCK, 0, st>>>(N, scal, z, p, first);
+    return end();
+}
+cudaError_t LinLaunch::jacobi_dot(long long N, const double* r, const double* diag, double* z,
+                                  double* part, int& nparts) {
+    nparts = stream_blocks(N);
+    begin("precond_jacobi");
+    k_jacobi_dot<<<nparts, LIN_BLOCK, 0, st>>>(N, r, diag, z, part);
+    return end();
+}
+cudaError_t LinLaunch::dot(long long N, const double* a, const double* b, double* part,
+                           int& nparts) {
+    nparts = stream_blocks(N);
+    begin("dot");
+    k_dot<<<nparts, LIN_BLOCK, 0, st>>>(N, a, b, part);
+    return end();
+}
+cudaError_t LinLaunch::cg_init(long long N, const double* b, double* r, double* x, double* part,
+                               int& nparts) {
+    nparts = stream_blocks(N);
+    begin("cg_init");
+    k_cg_init<<<nparts, LIN_BLOCK, 0, st>>>(N, b, r, x, part);
+    return end();
+}
+cudaError_t LinLaunch::reduce(const double* part, int n, double* scal, int op, int slot) {
+    begin("reduce");
+    k_reduce<<<1, RED_BLOCK, 0, st>>>(part, n, scal, op, slot);
+    return end();
+}
+
+template <typename T>
+cudaError_t LinLaunch::smooth(const Op<T>& A, const T* b, const T* xin, T* xout, T omega,
+                              int first) {
+    begin(sizeof(T) == 4 ? "mg_smooth_f32" : "mg_smooth_f64");
+    k_mg_smooth<T><<<stream_blocks(A.N), LIN_BLOCK, 0, st>>>(A, b, xin, xout, omega, first);
+    return end();
+}
+template <typename T>
+cudaError_t LinLaunch::restrict_res(const Op<T>& A, const T* b, const T* x, int cnx, int cny,
+                                    int cnz, T* bc) {
+    begin(sizeof(T) == 4 ? "mg_restrict_f32" : "mg_restrict_f64");
+    k_mg_restrict<T><<<stream_blocks((long long)cnx * cny * cnz), LIN_BLOCK, 0, st>>>(
+        A, b, x, cnx, cny, cnz, bc);
+    return end();
+}
+template <typename T>
+cudaError_t LinLaunch::prolong(int nx, int ny, int nz, int cnx, int cny, const T* xc, T* xf) {
+    begin(sizeof(T) == 4 ? "mg_prolong_f32" : "mg_prolong_f64");
+    k_mg_prolong<T><<<stream_blocks((long long)nx * ny * nz), LIN_BLOCK, 0, st>>>(nx, ny, nz, cnx,
+                                                                                cny, xc, xf);
+    return end();
+}
+template <typename TF, typename TC>
+cudaError_t LinLaunch::coarsen(const Op<TF>& A, int cnx, int cny, int cnz, TC* dc, TC* wx,
+                               TC* wy, TC* wz) {
+    begin("mg_coarsen");
+    k_mg_coarsen<TF, TC><<<stream_blocks((long long)cnx * cny * cnz), LIN_BLOCK, 0, st>>>(
+        A, cnx, cny, cnz, dc, wx, wy, wz);
+    return end();
+}
+template <typename T>
+cudaError_t LinLaunch::diag_faces(const Op<T>& A, T* diag) {
+    begin("mg_diag_faces");
+    k_mg_diag_faces<T><<<stream_blocks(A.N), LIN_BLOCK, 0, st>>>(A, diag);
+    return end();
+}
+cudaError_t LinLaunch::cast_op(const Op<double>& A, float* d, float* wx, float* wy, float* wz) {
+    begin("mg_cast_op");
+    k_cast_op<<<stream_blocks(A.N), LIN_BLOCK, 0, st>>>(A, d, wx, wy, wz);
+    return end();
+}
+cudaError_t LinLaunch::to_f32(long long N, const double* a, float* b) {
+    begin("mg_to_f32");
+    k_to_f32<<<stream_blocks(N), LIN_BLOCK, 0, st>>>(N, a, b);
+    return end();
+}
+cudaError_t LinLaunch::from_f32_dot(long long N, const float* x, const double* r, double* z,
+                                    double* part, int& nparts) {
+    nparts = stream_blocks(N);
+    begin("mg_from_f32_dot");
+    k_from_f32_dot<<<nparts, LIN_BLOCK, 0, st>>>(N, x, r, z, part);
+    return end();
+}
+
+template cudaError_t LinLaunch::smooth<double>(const Op<double>&, const double*, const double*,
+                                               double*, double, int);
+template cudaError_t LinLaunch::smooth<float>(const Op<float>&, const float*, const float*,
+                                              float*, float, int);
+template cudaError_t LinLaunch::restrict_res<double>(const Op<double>&, const double*,
+                                                     const double*, int, int, int, double*);
+template cudaError_t LinLaunch::restrict_res<float>(const Op<float>&, const float*, const float*,
+                                                    int, int, int, float*);
+template cudaError_t LinLaunch::prolong<double>(int, int, int, int, int, const double*, double*);
+template cudaError_t LinLaunch::prolong<float>(int, int, int, int, int, const float*, float*);
+template cudaError_t LinLaunch::coarsen<double, double>(const Op<double>&, int, int, int, double*,
+                                                        double*, double*, double*);
+template cudaError_t LinLaunch::coarsen<double, float>(const Op<double>&, int, int, int, float*,
+                                                       float*, float*, float*);
+template cudaError_t LinLaunch::coarsen<float, float>(const Op<float>&, int, int, int, float*,
+                                                      float*, float*, float*);
+template cudaError_t LinLaunch::diag_faces<double>(const Op<double>&, double*);
+template cudaError_t LinLaunch::diag_faces<float>(const Op<float>&, float*);
+
+}  // namespace rhi

@@ -1,0 +1,70 @@
+// Declarations of the CG / multigrid kernels' launchers (rhi_linear.cu).
+#pragma once
+
+#include "rhi_internal.cuh"
+
+namespace rhi {
+
+// One level's 7-point operator: (A x)_c = diag_c x_c - scale * sum_f W_f x_nb(f).
+template <typename T>
+struct Op {
+    int nx, ny, nz;
+    long long N;
+    int per[3];
+    const T* diag;
+    const T* W[3];       // lower-face coefficient per axis (0 on zero-flux boundary faces)
+    T scale;
+};
+
+// device scalar slots of the CG iteration
+enum { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RR, S_BREAK, S_TMP, S_NSCAL = 8 };
+enum { RED_SUM = 0, RED_ALPHA = 1, RED_BETA = 2 };
+
+// number of blocks of the grid-stride streaming kernels (= number of partial sums)
+int stream_blocks(long long N);
+
+// timing / counting hook called around every launch
+struct LaunchHook {
+    virtual void begin(const char* name) = 0;
+    virtual void end() = 0;
+    virtual ~LaunchHook() {}
+};
+
+struct LinLaunch {
+    cudaStream_t st;
+    LaunchHook* hook;
+    LinLaunch(cudaStream_t s, LaunchHook* h);
+    void begin(const char* name);
+    cudaError_t end();
+
+    cudaError_t matvec_dot(const Op<double>& A, const double* p, double* q, double* part,
+                           int& nparts);
+    cudaError_t cg_xr(long long N, const double* scal, double* x, double* r, const double* p,
+                      const double* q, double* part, int& nparts);
+    cudaError_t cg_p(long long N, const double* scal, const double* z, double* p, int first);
+    cudaError_t jacobi_dot(long long N, const double* r, const double* diag, double* z,
+                           double* part, int& nparts);
+    cudaError_t dot(long long N, const double* a, const double* b, double* part, int& nparts);
+    cudaError_t cg_init(long long N, const double* b, double* r, double* x, double* part,
+                        int& nparts);
+    cudaError_t reduce(const double* part, int n, double* scal, int op, int slot);
+
+    template <typename T>
+    cudaError_t smooth(const Op<T>& A, const T* b, const T* xin, T* xout, T omega, int first);
+    template <typename T>
+    cudaError_t restrict_res(const Op<T>& A, const T* b, const T* x, int cnx, int cny, int cnz,
+                             T* bc);
+    template <typename T>
+    cudaError_t prolong(int nx, int ny, int nz, int cnx, int cny, const T* xc, T* xf);
+    template <typename TF, typename TC>
+    cudaError_t coarsen(const Op<TF>& A, int cnx, int cny, int cnz, TC* dc, TC* wx, TC* wy,
+                        TC* wz);
+    template <typename T>
+    cudaError_t diag_faces(const Op<T>& A, T* diag);
+    cudaError_t cast_op(const Op<double>& A, float* d, float* wx, float* wy, float* wz);
+    cudaError_t to_f32(long long N, const double* a, float* b);
+    cudaError_t from_f32_dot(long long N, const float* x, const double* r, double* z,
+                             double* part, int& nparts);
+};
+
+}  // namespace rhi

@@ -1,0 +1,540 @@
+// Cell-local physics of the implicit step: opacity, limiter face coefficients, the fused
+// residual / Jacobian / Schur-elimination kernel, the Newton update with positivity cap, and
+// small state kernels.  All FP64.
+//
+// Reference passages: Sec. 3.2 (theta scheme, eqs. energy/chemistry/radiation_simplified,
+// operators mDE, mLe, mLn, mLE, residual eq. nonlinear_residual, RMS norm eq. rmsnorm),
+// Sec. 3.2.1 (Newton matrix eqs. jacobian_matrix / jacobian_submatrices, Schur steps (i)-(iii),
+// eqs. newton_system2, schur_components, step_ia), Sec. 3.2.2 (scalings eq. scalings),
+// Sec. 2.2 (limiter eq. limiter).
+#include "rhi_internal.cuh"
+
+namespace rhi {
+
+constexpr int CELL_BLOCK = 128;
+int cell_block_size() { return CELL_BLOCK; }
+
+// ---------------------------------------------------------------------------------------------
+// opacity kappa = sum_X sk_X n_X / a^3
+
+__global__ void k_kappa(const StepParams P, int ns, const double* __restrict__ n,
+                        double* __restrict__ kap) {
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= P.N) return;
+    double s = P.sk[0] * n[c];
+    if (ns == 3) s += P.sk[1] * n[P.N + c] + P.sk[2] * n[2 * P.N + c];
+    kap[c] = P.ia3 * s;
+}
+
+cudaError_t launch_kappa(const StepParams& P, int ns, const double* n, double* kap,
+                         cudaStream_t st) {
+    const int b = 256;
+    k_kappa<<<(unsigned)((P.N + b - 1) / b), b, 0, st>>>(P, ns, n, kap);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// face coefficients D / (a dx)^2 of each cell's three lower faces (eq. limiter)
+//
+// R = |E_b - E_a| / (a dx Ebar) floored at R_min; with q = max(|dE|, R_min a dx Ebar) and
+// s = a dx Ebar, D = c s (2 kappa s + q) / (6 kappa^2 s^2 + 3 kappa q s + q^2): one division.
+
+__device__ __forceinline__ double face_coef(const StepParams& P, double Ea, double Eb,
+                                            double ka, double kb) {
+    const double kap = 0.5 * (ka + kb);
+    if (P.limiter) {
+        const double s = 0.5 * (Ea + Eb) / P.inv_adx;          // a dx Ebar
+        const double q = fmax(fabs(Eb - Ea), P.R_min * s);
+        const double ks = kap * s;
+        const double num = C_LIGHT * s * (2.0 * ks + q);
+        const double den = 6.0 * ks * ks + 3.0 * ks * q + q * q;
+        return num / den * P.inv_a2dx2;
+    }
+    return C_LIGHT / (3.0 * fmax(kap, P.kappa_floor)) * P.inv_a2dx2;
+}
+
+__global__ void __launch_bounds__(256) k_faces(const StepParams P, const double* __restrict__ E,
+                                               const double* __restrict__ kap,
+                                               double* __restrict__ W) {
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= P.N) return;
+    int i, j, k;
+    cell_coords(P, c, i, j, k);
+    const Nbr b = neighbours(P, c, i, j, k);
+    const double Ec = E[c], kc = kap[c];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        double w = 0.0;
+        if (b.has_lo[ax]) w = face_coef(P, E[b.lo[ax]], Ec, kap[b.lo[ax]], kc);
+        W[ax * P.N + c] = w;
+    }
+}
+
+cudaError_t launch_faces(const StepParams& P, const double* E, const double* kap, double* W,
+                         cudaStream_t st) {
+    const int b = 256;
+    k_faces<<<(unsigned)((P.N + b - 1) / b), b, 0, st>>>(P, E, kap, W);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// local reaction operators and their derivatives (eqs. mLe, mLn, mLE, jacobian_submatrices)
+
+template <int NS>
+struct Local {
+    double L[NS + 1];          // L_e, L_n1 ..
+    double LE;                 // local part of the E operator
+    double dLx[NS + 1][NS + 1];
+    double dLxE[NS + 1];
+    double dLEx[NS + 1];
+    double dLEE;
+};
+
+template <int NS, bool JAC>
+__device__ __forceinline__ void local_model(const StepParams& P, double ec, const double (&n)[NS],
+                                            double E, double eh, double nH, double src,
+                                            double Tfix, Local<NS>& o) {
+    const double c = C_LIGHT, ia3 = P.ia3;
+    const double nHe = P.y_he * nH;
+    const double nHI = n[0];
+    double nHeI = 0.0, nHeII = 0.0;
+    if constexpr (NS == 3) { nHeI = n[1]; nHeII = n[2]; }
+    const double nHII = nH - nHI;
+    const double nHeIII = nHe - nHeI - nHeII;
+    const double ne = nHII + nHeII + 2.0 * nHeIII;
+    const double rho = M_H * (nH + 4.0 * nHe);
+    const double irho = 1.0 / rho;
+    const double e = eh + ec;
+    const double ntot = nH + nHe + ne;
+    double T, dT_dec, dT_dne;
+    if (P.isothermal) {
+        T = Tfix;
+        dT_dec = 0.0;
+        dT_dne = 0.0;
+    } else {
+        const double intot = 1.0 / ntot;
+        dT_dec = (GAMMA - 1.0) * rho / K_BOLTZ * intot;     // T is proportional to e
+        T = dT_dec * e;
+        dT_dne = -T * intot;                                // d n_tot = d n_e
+    }
+
+    // tabulated coefficients: bin = binary exponent and top mantissa bits of clamped T
+    const bool clamped = !(T >= 1.0 && T <= T_TABLE_MAX);
+    const double Tc = fmin(fmax(T, 1.0), T_TABLE_MAX);
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(Tc);
+    const int bin = (int)((bits >> (52 - TABLE_BITS)) - (1023ull << TABLE_BITS));
+    const double Ti = __longlong_as_double((long long)(bits & ~((1ull << (52 - TABLE_BITS)) - 1ull)));
+    const double dTi = Tc - Ti;
+    const double2* row = P.table + (long long)bin * NRATES;
+    double k[NRATES], dk[NRATES];
+#pragma unroll
+    for (int r = 0; r < NRATES; ++r) {
+        const bool need = (NS == 3) || r == R_ALPHA_HII || r == R_BETA_HI || r == R_COOL_HI ||
+                          r == R_COOL_HII;
+        if (need) {
+            const double2 v = __ldg(row + r);
+            k[r] = fma(v.y, dTi, v.x);
+            dk[r] = clamped ? 0.0 : v.y;
+        } else {
+            k[r] = 0.0;
+            dk[r] = 0.0;
+        }
+    }
+    const double C = k[R_COOL_HI] * nHI + k[R_COOL_HII] * nHII + k[R_COOL_HEI] * nHeI +
+                     k[R_COOL_HEII] * nHeII + k[R_COOL_HEIII] * nHeIII;
+
+    const double cE = c * E * ia3;
+    const double GHI = P.pg[0] * cE, GHeI = P.pg[1] * cE, GHeII = P.pg[2] * cE;
+    const double ne3 = ia3 * ne;
+    const double B0 = k[R_BETA_HI] * nHI - k[R_ALPHA_HII] * nHII;
+    o.L[1] = GHI * nHI + ne3 * B0;
+    double B1 = 0.0, B2 = 0.0;
+    if constexpr (NS == 3) {
+        B1 = k[R_BETA_HEI] * nHeI - k[R_ALPHA_HEII] * nHeII;
+        B2 = (k[R_BETA_HEII] + k[R_ALPHA_HEII]) * nHeII - k[R_BETA_HEI] * nHeI -
+             k[R_ALPHA_HEIII] * nHeIII;
+        o.L[2] = GHeI * nHeI + ne3 * B1;
+        o.L[3] = GHeII * nHeII - GHeI * nHeI + ne3 * B2;
+    }
+    const double heat = P.ph[0] * nHI + P.ph[1] * nHeI + P.ph[2] * nHeII;
+    const double G = cE * heat * irho;
+    const double Lam = ne3 * C * irho;
+    o.L[0] = P.isothermal ? 0.0 : (2.0 * P.adot_a * ec - G + Lam);
+    const double kap = ia3 * (P.sk[0] * nHI + P.sk[1] * nHeI + P.sk[2] * nHeII);
+    o.LE = P.m_grey * P.adot_a * E - src + c * kap * E;
+    if constexpr (!JAC) return;
+
+    const double dne[3] = {-1.0, -2.0, -1.0};
+    const double dCdn[3] = {k[R_COOL_HI] - k[R_COOL_HII], k[R_COOL_HEI] - k[R_COOL_HEIII],
+                            k[R_COOL_HEII] - k[R_COOL_HEIII]};
+    const double dCdT = dk[R_COOL_HI] * nHI + dk[R_COOL_HII] * nHII + dk[R_COOL_HEI] * nHeI +
+                        dk[R_COOL_HEII] * nHeII + dk[R_COOL_HEIII] * nHeIII;
+    // energy row
+    if (P.isothermal) {
+#pragma unroll
+        for (int s = 0; s <= NS; ++s) o.dLx[0][s] = 0.0;
+        o.dLxE[0] = 0.0;
+    } else {
+        o.dLx[0][0] = 2.0 * P.adot_a + ne3 * dCdT * dT_dec * irho;
+#pragma unroll
+        for (int j = 0; j < NS; ++j)
+            o.dLx[0][1 + j] = -cE * P.ph[j] * irho +
+                              ia3 * irho * (dne[j] * C + ne * dCdn[j] + ne * dCdT * dT_dne * dne[j]);
+        o.dLxE[0] = -c * ia3 * heat * irho;
+    }
+    // species rows: d/dx [A + ia3 n_e B] = dA/dx + ia3 (dn_e/dx B + n_e dB/dx|_T + n_e dB/dT dT/dx)
+    const double dBdT0 = dk[R_BETA_HI] * nHI - dk[R_ALPHA_HII] * nHII;
+    o.dLx[1][0] = ne3 * dBdT0 * dT_dec;
+    o.dLx[1][1] = GHI + ia3 * (dne[0] * B0 + ne * (k[R_BETA_HI] + k[R_ALPHA_HII]) +
+                               ne * dBdT0 * dT_dne * dne[0]);
+    o.dLxE[1] = c * P.pg[0] * ia3 * nHI;
+    if constexpr (NS == 3) {
+        o.dLx[1][2] = ia3 * (dne[1] * B0 + ne * dBdT0 * dT_dne * dne[1]);
+        o.dLx[1][3] = ia3 * (dne[2] * B0 + ne * dBdT0 * dT_dne * dne[2]);
+        const double dBdT1 = dk[R_BETA_HEI] * nHeI - dk[R_ALPHA_HEII] * nHeII;
+        o.dLx[2][0] = ne3 * dBdT1 * dT_dec;
+        o.dLx[2][1] = ia3 * (dne[0] * B1 + ne * dBdT1 * dT_dne * dne[0]);
+        o.dLx[2][2] = GHeI + ia3 * (dne[1] * B1 + ne * k[R_BETA_HEI] + ne * dBdT1 * dT_dne * dne[1]);
+        o.dLx[2][3] = ia3 * (dne[2] * B1 - ne * k[R_ALPHA_HEII] + ne * dBdT1 * dT_dne * dne[2]);
+        o.dLxE[2] = c * P.pg[1] * ia3 * nHeI;
+        const double dBdT2 = (dk[R_BETA_HEII] + dk[R_ALPHA_HEII]) * nHeII - dk[R_BETA_HEI] * nHeI -
+                             dk[R_ALPHA_HEIII] * nHeIII;
+        o.dLx[3][0] = ne3 * dBdT2 * dT_dec;
+        o.dLx[3][1] = ia3 * (dne[0] * B2 + ne * dBdT2 * dT_dne * dne[0]);
+        o.dLx[3][2] = -GHeI + ia3 * (dne[1] * B2 + ne * (-k[R_BETA_HEI] + k[R_ALPHA_HEIII]) +
+                                     ne * dBdT2 * dT_dne * dne[1]);
+        o.dLx[3][3] = GHeII + ia3 * (dne[2] * B2 +
+                                     ne * (k[R_BETA_HEII] + k[R_ALPHA_HEII] + k[R_ALPHA_HEIII]) +
+                                     ne * dBdT2 * dT_dne * dne[2]);
+        o.dLxE[3] = c * ia3 * (P.pg[2] * nHeII - P.pg[1] * nHeI);
+    }
+    o.dLEx[0] = 0.0;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) o.dLEx[1 + j] = c * ia3 * P.sk[j] * E;
+    o.dLEE = P.m_grey * P.adot_a + c * kap;
+}
+
+// Gaussian elimination with partial pivoting for two right-hand sides (step (i), eq. step_ia)
+template <int NM>
+__device__ __forceinline__ void lu_solve2(double (&A)[NM][NM], double (&y)[NM], double (&z)[NM]) {
+    double inv[NM];
+#pragma unroll
+    for (int k = 0; k < NM; ++k) {
+        int p = k;
+        double best = fabs(A[k][k]);
+#pragma unroll
+        for (int r = k + 1; r < NM; ++r) {
+            const double v = fabs(A[r][k]);
+            if (v > best) { best = v; p = r; }
+        }
+#pragma unroll
+        for (int r = k + 1; r < NM; ++r) {
+            if (r == p) {
+#pragma unroll
+                for (int c = k; c < NM; ++c) { const double t = A[k][c]; A[k][c] = A[r][c]; A[r][c] = t; }
+                double t = y[k]; y[k] = y[r]; y[r] = t;
+                t = z[k]; z[k] = z[r]; z[r] = t;
+            }
+        }
+        inv[k] = 1.0 / A[k][k];
+#pragma unroll
+        for (int r = k + 1; r < NM; ++r) {
+            const double m = A[r][k] * inv[k];
+#pragma unroll
+            for (int c = k + 1; c < NM; ++c) A[r][c] -= m * A[k][c];
+            y[r] -= m * y[k];
+            z[r] -= m * z[k];
+        }
+    }
+#pragma unroll
+    for (int k = NM - 1; k >= 0; --k) {
+        double sy = y[k], sz = z[k];
+#pragma unroll
+        for (int c = k + 1; c < NM; ++c) { sy -= A[k][c] * y[c]; sz -= A[k][c] * z[c]; }
+        y[k] = sy * inv[k];
+        z[k] = sz * inv[k];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// fused residual / Jacobian / Schur kernel
+//
+// MODE_PREP:         U = (0, n^n, E^n); writes g^n = U^n + dt (theta - 1) L(U^n), f(U^n),
+//                    and the Schur system at U^n.
+// MODE_ITER:         U given; reads g; writes f(U) and the Schur system at U.
+// MODE_PREP_PREDICT: writes g^n and the explicit predictor U^n - dt L(U^n) (capped).
+
+template <int NS, int MODE>
+__global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const PhysBuffers B) {
+    constexpr int NM = NS + 1, NV = NS + 2;
+    const long long c = blockIdx.x * (long long)CELL_BLOCK + threadIdx.x;
+    const long long N = P.N;
+    double fsq = 0.0;
+    if (c < N) {
+        int i, j, k;
+        cell_coords(P, c, i, j, k);
+        const Nbr nb = neighbours(P, c, i, j, k);
+        const bool prep = (MODE != MODE_ITER);
+        const double* En = prep ? B.E_n : B.E;
+        const double* nn = prep ? B.n_n : B.n;
+        const double E = En[c];
+        double n[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) n[s] = nn[s * N + c];
+        const double ec = (prep || B.ec == nullptr) ? 0.0 : B.ec[c];
+        const double eh = B.eh[c], nH = B.nH[c], src = B.src[c];
+        const double Tfix = P.isothermal ? B.Tiso[c] : 0.0;
+
+        // diffusion: sum over faces W (E_c - E_nb), with W frozen (lagged D)
+        double Dterm = 0.0, Wsum = 0.0;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const double wlo = B.W[ax * N + c];
+            const double whi = nb.has_hi[ax] ? B.W[ax * N + nb.hi[ax]] : 0.0;
+            Dterm += wlo * (E - En[nb.lo[ax]]) + whi * (E - En[nb.hi[ax]]);
+            Wsum += wlo + whi;
+        }
+
+        Local<NS> lo;
+        local_model<NS, MODE != MODE_PREP_PREDICT>(P, ec, n, E, eh, nH, src, Tfix, lo);
+        double Lf[NV];
+#pragma unroll
+        for (int v = 0; v <= NS; ++v) Lf[v] = lo.L[v];
+        Lf[NV - 1] = Dterm + lo.LE;
+        double U[NV];
+        U[0] = ec;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) U[1 + s] = n[s];
+        U[NV - 1] = E;
+        double g[NV];
+        if (prep) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                g[v] = U[v] + P.dtm1 * Lf[v];
+                B.g[v * N + c] = g[v];
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) g[v] = B.g[v * N + c];
+        }
+
+        if (MODE == MODE_PREP_PREDICT) {
+            // explicit Euler predictor U^n - dt L(U^n) (eq. explicit_predictor), positivity cap
+            double d[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) d[v] = -P.dt * Lf[v];
+            double cap = 1.0;
+            auto bound = [&](double q, double dq, double tiny) {
+                if (dq < -tiny) cap = fmin(cap, fmax(P.tau * q / (-dq), 0.0));
+            };
+            bound(eh + ec, d[0], 0.0);
+            bound(E, d[NV - 1], 0.0);
+            bound(n[0], d[1], 1e-13 * nH);
+            bound(nH - n[0], -d[1], 1e-13 * nH);
+            if constexpr (NS == 3) {
+                const double nHe = P.y_he * nH;
+                bound(n[1], d[2], 1e-13 * nHe);
+                bound(n[2], d[3], 1e-13 * nHe);
+                bound(nHe - n[1] - n[2], -d[2] - d[3], 1e-13 * nHe);
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) B.U0[v * N + c] = U[v] + cap * d[v];
+        } else {
+            // scalings of the local unknowns (e_c, n_1 ..) and their inverses
+            double us[NM], ius[NM];
+#pragma unroll
+            for (int r = 0; r < NM; ++r) {
+                us[r] = r == 0 ? P.u_e : P.u_n;
+                ius[r] = r == 0 ? P.iu_e : P.iu_n;
+            }
+            // scaled residual (eq. nonlinear_residual / eq. scalings)
+            double fs[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const double f = U[v] + P.dth * Lf[v] - g[v];
+                fs[v] = f * (v == NV - 1 ? P.iu_E : (v == 0 ? P.iu_e : P.iu_n));
+                fsq += fs[v] * fs[v];
+                if (B.f_out) B.f_out[v * N + c] = fs[v];
+            }
+            // scaled local blocks (eq. schur_components)
+            double M[NM][NM], y[NM], z[NM], Lr[NM];
+#pragma unroll
+            for (int r = 0; r < NM; ++r) {
+#pragma unroll
+                for (int s = 0; s < NM; ++s)
+                    M[r][s] = (r == s ? 1.0 : 0.0) + P.dth * lo.dLx[r][s] * us[s] * ius[r];
+                z[r] = P.dth * lo.dLxE[r] * P.u_E * ius[r];
+                Lr[r] = P.dth * lo.dLEx[r] * us[r] * P.iu_E;
+                y[r] = fs[r];
+            }
+            const double Dloc = 1.0 + P.dth * lo.dLEE;
+            lu_solve2<NM>(M, y, z);                         // y = M^-1 f_M, z = M^-1 U
+            double LMU = 0.0, LMf = 0.0;
+#pragma unroll
+            for (int r = 0; r < NM; ++r) { LMU += Lr[r] * z[r]; LMf += Lr[r] * y[r]; }
+            B.diag[c] = Dloc - LMU + P.dth * Wsum;
+            B.rhs[c] = LMf - fs[NV - 1];
+#pragma unroll
+            for (int r = 0; r < NM; ++r) {
+                B.fMt[r * N + c] = y[r];
+                B.MiU[r * N + c] = z[r];
+            }
+        }
+    }
+    if (MODE != MODE_PREP_PREDICT) {
+        const double s = block_sum<CELL_BLOCK>(fsq);
+        if (threadIdx.x == 0) B.partials[blockIdx.x] = s;
+    }
+}
+
+cudaError_t launch_cell(const StepParams& P, int ns, int mode, const PhysBuffers& B,
+                        int nblocks, cudaStream_t st) {
+    const dim3 g(nblocks), b(CELL_BLOCK);
+    if (ns == 1) {
+        if (mode == MODE_PREP) k_cell<1, MODE_PREP><<<g, b, 0, st>>>(P, B);
+        else if (mode == MODE_ITER) k_cell<1, MODE_ITER><<<g, b, 0, st>>>(P, B);
+        else k_cell<1, MODE_PREP_PREDICT><<<g, b, 0, st>>>(P, B);
+    } else {
+        if (mode == MODE_PREP) k_cell<3, MODE_PREP><<<g, b, 0, st>>>(P, B);
+        else if (mode == MODE_ITER) k_cell<3, MODE_ITER><<<g, b, 0, st>>>(P, B);
+        else k_cell<3, MODE_PREP_PREDICT><<<g, b, 0, st>>>(P, B);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Newton update: step (iii) recovery, positivity cap, line-search fraction, new opacity
+
+template <int NS>
+__global__ void __launch_bounds__(256) k_update(const StepParams P, double lam,
+                                                const double* __restrict__ ec0,
+                                                const double* __restrict__ n0,
+                                                const double* __restrict__ E0,
+                                                const double* __restrict__ eh,
+                                                const double* __restrict__ nHa,
+                                                const double* __restrict__ sE,
+                                                const double* __restrict__ fMt,
+                                                const double* __restrict__ MiU,
+                                                double* __restrict__ ec1, double* __restrict__ n1,
+                                                double* __restrict__ E1,
+                                                double* __restrict__ kap1) {
+    constexpr int NM = NS + 1;
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long N = P.N;
+    if (c >= N) return;
+    const double se = sE[c];
+    double s[NM];
+#pragma unroll
+    for (int r = 0; r < NM; ++r) s[r] = (-fMt[r * N + c] - MiU[r * N + c] * se) * (r == 0 ? P.u_e : P.u_n);
+    const double sEp = se * P.u_E;
+    const double ec = ec0 ? ec0[c] : 0.0;
+    double n[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) n[j] = n0[j * N + c];
+    const double E = E0[c], nH = nHa[c];
+    double cap = 1.0;
+    auto bound = [&](double q, double dq, double tiny) {
+        if (dq < -tiny) cap = fmin(cap, fmax(P.tau * q / (-dq), 0.0));
+    };
+    bound(eh[c] + ec, s[0], 0.0);
+    bound(E, sEp, 0.0);
+    bound(n[0], s[1], 1e-13 * nH);
+    bound(nH - n[0], -s[1], 1e-13 * nH);
+    if constexpr (NS == 3) {
+        const double nHe = P.y_he * nH;
+        bound(n[1], s[2], 1e-13 * nHe);
+        bound(n[2], s[3], 1e-13 * nHe);
+        bound(nHe - n[1] - n[2], -s[2] - s[3], 1e-13 * nHe);
+    }
+    const double fr = fmin(lam, cap);
+    ec1[c] = ec + fr * s[0];
+    double ksum = 0.0;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        const double v = n[j] + fr * s[1 + j];
+        n1[j * N + c] = v;
+        ksum += P.sk[j] * v;
+    }
+    E1[c] = E + fr * sEp;
+    kap1[c] = P.ia3 * ksum;
+}
+
+cudaError_t launch_update(const StepParams& P, int ns, double lam, const double* ec0,
+                          const double* n0, const double* E0, const double* eh,
+                          const double* nH, const double* sE, const double* fMt,
+                          const double* MiU, double* ec1, double* n1, double* E1,
+                          double* kap1, cudaStream_t st) {
+    const int b = 256;
+    const unsigned g = (unsigned)((P.N + b - 1) / b);
+    if (ns == 1)
+        k_update<1><<<g, b, 0, st>>>(P, lam, ec0, n0, E0, eh, nH, sE, fMt, MiU, ec1, n1, E1, kap1);
+    else
+        k_update<3><<<g, b, 0, st>>>(P, lam, ec0, n0, E0, eh, nH, sE, fMt, MiU, ec1, n1, E1, kap1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// small state kernels
+
+__global__ void k_finalize(long long N, const double* __restrict__ ec, double* __restrict__ eh) {
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c < N) eh[c] += ec[c];           // e^{n+1} = e_h + e_c (Sec. 3.1)
+}
+
+cudaError_t launch_finalize(const StepParams& P, int, const double* ec, double* eh,
+                            cudaStream_t st) {
+    const int b = 256;
+    k_finalize<<<(unsigned)((P.N + b - 1) / b), b, 0, st>>>(P.N, ec, eh);
+    return cudaGetLastError();
+}
+
+__global__ void k_temperature(const StepParams P, int ns, const double* __restrict__ e,
+                              const double* __restrict__ n, const double* __restrict__ nHa,
+                              double* __restrict__ T) {
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= P.N) return;
+    const double nH = nHa[c], nHe = P.y_he * nH;
+    const double nHI = n[c];
+    const double nHeI = ns == 3 ? n[P.N + c] : 0.0, nHeII = ns == 3 ? n[2 * P.N + c] : 0.0;
+    const double ne = (nH - nHI) + nHeII + 2.0 * (nHe - nHeI - nHeII);
+    const double rho = M_H * (nH + 4.0 * nHe);
+    T[c] = (GAMMA - 1.0) * rho * e[c] / (K_BOLTZ * (nH + nHe + ne));
+}
+
+cudaError_t launch_temperature(const StepParams& P, int ns, const double* e, const double* n,
+                               const double* nH, double* T, cudaStream_t st) {
+    const int b = 256;
+    k_temperature<<<(unsigned)((P.N + b - 1) / b), b, 0, st>>>(P, ns, e, n, nH, T);
+    return cudaGetLastError();
+}
+
+__global__ void k_check_state(const StepParams P, int ns, const double* __restrict__ E,
+                              const double* __restrict__ e, const double* __restrict__ n,
+                              const double* __restrict__ nHa, int* bad) {
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= P.N) return;
+    const double nH = nHa[c], nHe = P.y_he * nH;
+    const double nHI = n[c];
+    const double nHeI = ns == 3 ? n[P.N + c] : 0.0, nHeII = ns == 3 ? n[2 * P.N + c] : 0.0;
+    const bool ok = (E[c] > 0.0) && (e[c] > 0.0) && (nH > 0.0) && (nHI >= 0.0) &&
+                    (nH - nHI >= 0.0) && (nHeI >= 0.0) && (nHeII >= 0.0) &&
+                    (nHe - nHeI - nHeII >= 0.0) && isfinite(E[c]) && isfinite(e[c]) &&
+                    isfinite(nH);
+    if (!ok) atomicOr(bad, 1);
+}
+
+cudaError_t launch_check_state(const StepParams& P, int ns, const double* E, const double* e,
+                               const double* n, const double* nH, int* bad, cudaStream_t st) {
+    const int b = 256;
+    k_check_state<<<(unsigned)((P.N + b - 1) / b), b, 0, st>>>(P, ns, E, e, n, nH, bad);
+    return cudaGetLastError();
+}
+
+__global__ void k_deposit(long long cell, double value, double* src) { src[cell] += value; }
+
+cudaError_t launch_deposit(long long cell, double value, double* src, cudaStream_t st) {
+    k_deposit<<<1, 1, 0, st>>>(cell, value, src);
+    return cudaGetLastError();
+}
+
+}  // namespace rhi

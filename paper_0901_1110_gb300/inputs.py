@@ -87,7 +87,8 @@ def gaussian_random_field(shape, seed, slope=-2.0):
     amp[nz] = k[nz] ** (slope / 2.0)
     g = np.fft.irfftn(np.fft.rfftn(w) * amp, s=shape, axes=(0, 1, 2))
     g -= g.mean()
-    return g / g.std()
+    sd = g.std()
+    return g / sd if sd > 0 else g        # a single cell has no k > 0 mode
 
 
 def uniform_h(n=32, box=1.0 * MPC, nH=1e-3, T0=100.0, x0=1e-4, E0=1e-20, ndot=5e48,
