@@ -204,10 +204,10 @@ def run_form(rhi, w, torch, steps, warmup, precond, profile):
     return s, ms, agg, kt
 
 
-def e2e_form(rhi, w, torch, steps, precond):
-    """Same metric through the public API with host buffers: each step copies the step's
-    inputs (E, e, n, n_H and the point-source list) from pinned host memory, runs the step and
-    reads the state (E, e, n) back into pinned host memory."""
+def e2e_form(rhi, w, torch, steps, warmup, precond):
+    """Same metric through the public API with host buffers: each timed step copies the
+    step's inputs (E, e, n, n_H and the point-source list) from pinned host memory, runs the
+    step and reads the state (E, e, n) back into pinned host memory."""
     s = rhi.solver_for_workload(w, precond=precond, mg_levels=6, theta=1.0)
     N = w.N
     pin = lambda m: torch.empty(m, dtype=torch.float64, pin_memory=True).numpy()
@@ -215,6 +215,10 @@ def e2e_form(rhi, w, torch, steps, precond):
     E, e, n, nH = pin(N), pin(N), pin(w.ns * N), pin(N)
     E[:] = st["E"]; e[:] = st["e"]; n[:] = st["n"].ravel(); nH[:] = w.nH.ravel()
     oE, oe, on = pin(N), pin(N), pin(w.ns * N)
+    # the same step indices as the device-timed region: warm-up steps first, untimed
+    for _ in range(warmup):
+        s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol)
+    s.get_state(E, e, n)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
@@ -241,6 +245,9 @@ def main():
     ap.add_argument("--impl", default="rhi")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forms", default="plain_fp64,mixed_fp32mg",
+                    help="comma list of forms to time (the last one is the headline)")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -273,8 +280,10 @@ def main():
 
     # plain FP64 form (FP64 multigrid), then the mixed form (FP32 multigrid) as headline
     forms = {}
-    for name, pc in (("plain_fp64", rhi.RHI_PRECOND_MG_FP64),
-                     ("mixed_fp32mg", rhi.RHI_PRECOND_MG_FP32)):
+    codes = {"plain_fp64": rhi.RHI_PRECOND_MG_FP64, "mixed_fp32mg": rhi.RHI_PRECOND_MG_FP32}
+    order = [f for f in args.forms.split(",") if f]
+    for name in order:
+        pc = codes[name]
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -290,7 +299,7 @@ def main():
         del s
         torch.cuda.empty_cache()
 
-    head = forms["mixed_fp32mg"]
+    head = forms[order[-1]]
     ms_step = head["ms"] / args.steps
     value = world * w.N * args.steps / (head["ms"] * 1e-3)
 
@@ -311,7 +320,7 @@ def main():
             ms_k, c_k = kt[k]
             lin[k] = ALG_BYTES[k] * w.N / (ms_k / c_k * 1e-3) / 1e9 / hbm_peak
 
-    plain = forms["plain_fp64"]
+    plain = forms.get("plain_fp64", head)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -338,10 +347,11 @@ def main():
         "hbm_frac_linear_kernels": lin,
     }
     if rank == 0:
-        e2e_val, h2d, d2h = e2e_form(rhi, w, torch, max(2, args.steps // 2),
-                                     rhi.RHI_PRECOND_MG_FP32)
-        line["e2e"] = {"value": world * e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h}
+        if not args.no_e2e:
+            e2e_val, h2d, d2h = e2e_form(rhi, w, torch, args.steps, args.warmup,
+                                         codes[order[-1]])
+            line["e2e"] = {"value": world * e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                           "d2h_bytes_per_step": d2h}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_sample()
         print(json.dumps(line), flush=True)
