@@ -169,6 +169,23 @@ int rhi_precond_apply(rhi_handle h, const double* r, double* z, int on_device);
 int rhi_set_profiling(rhi_handle h, int on);
 int rhi_kernel_times(rhi_handle h, int max, char* names, double* total_ms, int* launches);
 
+/* Allocation-free RMS norm (no counterpart in the paper; an addition for callers that may
+   not allocate device memory, such as code running while a stream is captured into a CUDA
+   graph, where cudaMalloc is not allowed, or an application that owns all device memory
+   through its own pool).  Computes out[0] = sqrt(sum_{i<n} v[i]^2 / count), the norm of
+   eq. rmsnorm when v holds the scaled residual and count = N (N_s + 2).
+   v (n doubles) and out (1 double) are device pointers owned by the caller; stream is a
+   cudaStream_t (NULL: legacy default stream); the call only enqueues work and returns.
+   Scratch: a static device array of RHI_NOALLOC_MAX_COUNT / 256 doubles (1 MiB) that every
+   GPU loading the library holds until the process exits; nothing is allocated.  n above
+   RHI_NOALLOC_MAX_COUNT is rejected with RHI_ERR_ARG before any launch.  The first call on a
+   device looks up the scratch address for that device (make it before any stream capture).
+   Every call overwrites the whole scratch it uses and nothing in it needs to start at zero,
+   but calls that overlap on the GPU (different streams or host threads) race on it. */
+#define RHI_NOALLOC_MAX_COUNT 33554432LL
+int rhi_rms_norm_noalloc(const double* v, long long n, long long count, double* out,
+                         void* stream);
+
 const char* rhi_last_error(rhi_handle h);
 const char* rhi_status_string(int status);
 void rhi_destroy(rhi_handle h);

@@ -64,6 +64,7 @@ _SIGS = {
     "rhi_precond_apply": (C.c_int, [_P, _P, _P, C.c_int]),
     "rhi_set_profiling": (C.c_int, [_P, C.c_int]),
     "rhi_kernel_times": (C.c_int, [_P, C.c_int, C.c_char_p, _D, C.POINTER(C.c_int)]),
+    "rhi_rms_norm_noalloc": (C.c_int, [_P, C.c_longlong, C.c_longlong, _P, _P]),
     "rhi_last_error": (C.c_char_p, [_P]),
     "rhi_status_string": (C.c_char_p, [C.c_int]),
     "rhi_destroy": (None, [_P]),
@@ -111,6 +112,15 @@ def rhi_grey_constants(spectrum, param, n_species):
     if rc:
         raise RhiError(rc, "rhi_grey_constants")
     return dict(sk=np.array(sk[:]), pgam=np.array(pg[:]), ph=np.array(ph[:]), eps=eps.value)
+
+
+RHI_NOALLOC_MAX_COUNT = 33554432
+
+
+def rhi_rms_norm_noalloc(v_ptr, n, count, out_ptr, stream=None):
+    """Allocation-free RMS norm of n doubles at device address v_ptr into the device double at
+    out_ptr (enqueued on `stream`); returns the status code."""
+    return lib().rhi_rms_norm_noalloc(v_ptr, n, count, out_ptr, stream)
 
 
 def rhi_status_string(code):

@@ -16,7 +16,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librhi.so")
 
-SOURCES = ["rhi_host.cu", "rhi_closure.cu", "rhi_physics.cu", "rhi_linear.cu"]
+SOURCES = ["rhi_host.cu", "rhi_closure.cu", "rhi_physics.cu", "rhi_linear.cu",
+           "rhi_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]
