@@ -115,9 +115,7 @@ def _oracle_subbox(n, nsrc):
     """A sub-box of the 256^3 recipe (same generator, same cell size) as an oracle problem."""
     from paper_0901_1110_gb300 import inputs
     from oracle import closure as cl, model as md
-    w = inputs.lognormal_hhe((n, n, n), box=1.0 * inputs.MPC * n / 256, seed=0, nsrc=nsrc,
-                             dt=5e12)
-    w.theta = 1.0
+    w = inputs.config_lognormal(n, nsrc=nsrc, seed=0, box=1.0 * inputs.MPC * n / 256)
     grey = cl.grey_constants(*w.spectrum, w.ns)
     p = md.Problem(nx=n, ny=n, nz=n, dx=w.dx, ns=w.ns, nH=w.nH, grey=grey, y_he=w.y_he,
                    src=cl.deposit_sources(w.nH.shape, w.dx, w.src_ijk, w.src_rate, grey["eps"]),
@@ -178,24 +176,33 @@ def cpu_baseline_sample():
                       "(numpy/scipy; BLAS threads over the host cores)"}
 
 
-def run_form(rhi, w, torch, steps, warmup, precond, profile):
+def run_form(rhi, w, torch, steps, warmup, precond, profile, limiter_jacobian=0,
+             max_newton=200):
     """Times `steps` implicit steps after `warmup` with CUDA events on the library's stream."""
     stream = torch.cuda.Stream()
     s = rhi.solver_for_workload(w, stream=stream.cuda_stream, precond=precond, mg_levels=6,
-                                theta=1.0)
+                                theta=1.0, limiter_jacobian=limiter_jacobian,
+                                max_newton=max_newton)
     for _ in range(warmup):
-        s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol)
+        rc = s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol, check=False)
+        if rc:
+            st = s.stats()
+            raise RuntimeError(f"warm-up step failed ({rc}): newton_its={st['newton_its']} "
+                               f"residuals={st['res_history']}")
     s.set_profiling(profile)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     agg = dict(newton_its=0, pcg_its=0, vcycles=0, launches=0, backtracks=0)
     e0.record(stream)
+    hist = []
     for _ in range(steps):
         s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol)
         st = s.stats()
         for k in agg:
             agg[k] += st[k]
+        hist.append(st["res_history"])
+    agg["res_history_last"] = hist[-1]
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -204,11 +211,12 @@ def run_form(rhi, w, torch, steps, warmup, precond, profile):
     return s, ms, agg, kt
 
 
-def e2e_form(rhi, w, torch, steps, warmup, precond):
+def e2e_form(rhi, w, torch, steps, warmup, precond, limiter_jacobian=0, max_newton=200):
     """Same metric through the public API with host buffers: each timed step copies the
     step's inputs (E, e, n, n_H and the point-source list) from pinned host memory, runs the
     step and reads the state (E, e, n) back into pinned host memory."""
-    s = rhi.solver_for_workload(w, precond=precond, mg_levels=6, theta=1.0)
+    s = rhi.solver_for_workload(w, precond=precond, mg_levels=6, theta=1.0,
+                                limiter_jacobian=limiter_jacobian, max_newton=max_newton)
     N = w.N
     pin = lambda m: torch.empty(m, dtype=torch.float64, pin_memory=True).numpy()
     st = w.state()
@@ -240,7 +248,7 @@ def e2e_form(rhi, w, torch, steps, warmup, precond):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rhi")
     ap.add_argument("--n", type=int, default=256)
@@ -248,6 +256,9 @@ def main():
     ap.add_argument("--forms", default="plain_fp64,mixed_fp32mg",
                     help="comma list of forms to time (the last one is the headline)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--max-newton", type=int, default=200)
+    ap.add_argument("--limiter-jacobian", type=int, default=0,
+                    help="1: keep dD/dE in the Newton matrix (BiCGStab)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -273,14 +284,13 @@ def main():
 
     n = args.n
     nsrc = max(1, round(64 * (n / 256) ** 3))
-    w = inputs.lognormal_hhe((n, n, n), seed=rank, nsrc=nsrc, dt=5e12,
-                             name=f"lognormal_hhe_{n}")
-    w.theta = 1.0
+    w = inputs.config_lognormal(n, nsrc=nsrc, seed=rank)
     hbm_peak, peak_src = load_peaks()
 
     # plain FP64 form (FP64 multigrid), then the mixed form (FP32 multigrid) as headline
     forms = {}
     codes = {"plain_fp64": rhi.RHI_PRECOND_MG_FP64, "mixed_fp32mg": rhi.RHI_PRECOND_MG_FP32}
+    ljac = {"plain_fp64": args.limiter_jacobian, "mixed_fp32mg": args.limiter_jacobian}
     order = [f for f in args.forms.split(",") if f]
     for name in order:
         pc = codes[name]
@@ -289,7 +299,8 @@ def main():
         torch.cuda.synchronize()
         clk = ClockSampler(local)
         clk.start()
-        s, ms, agg, kt = run_form(rhi, w, torch, args.steps, args.warmup, pc, profile=True)
+        s, ms, agg, kt = run_form(rhi, w, torch, args.steps, args.warmup, pc, profile=True,
+                                  limiter_jacobian=ljac[name], max_newton=args.max_newton)
         clocks = clk.stop()
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         if dist:
@@ -327,7 +338,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"lognormal_hhe {n}^3 H+He, sigma_ln=1, P(k)~k^-2, {nsrc} sources "
                                "(median 1e49/s), T_B=1e5 K, dt=5e12 s, theta=1, Newton tol "
-                               "1e-8, PCG tol 1e-10",
+                               "1e-8 (u_E = 1e-16), PCG tol 1e-10",
                    "form": "FP64 Newton/Schur/CG + FP32 multigrid V-cycle (6 levels, 2+2 "
                            "Jacobi, 16 coarse sweeps)",
                    "parallelism": "replicas" if world > 1 else "1 GPU",
@@ -335,8 +346,11 @@ def main():
         "roofline": roof,
         "plain_fp64": {"value": world * w.N * args.steps / (plain["ms"] * 1e-3),
                        "ms_per_step": plain["ms"] / args.steps,
-                       **{k: v / args.steps for k, v in plain["agg"].items()}},
-        "iterations_per_step": {k: v / args.steps for k, v in head["agg"].items()},
+                       **{k: v / args.steps for k, v in plain["agg"].items()
+                          if k != "res_history_last"}},
+        "iterations_per_step": {k: v / args.steps for k, v in head["agg"].items()
+                                if k != "res_history_last"},
+        "newton_residuals_last_step": head["agg"]["res_history_last"],
         "gpu_launches": head["agg"]["launches"],
         "clocks": head["clocks"],
         "kernel_ms_per_step": {k: v[0] / args.steps
@@ -349,7 +363,7 @@ def main():
     if rank == 0:
         if not args.no_e2e:
             e2e_val, h2d, d2h = e2e_form(rhi, w, torch, args.steps, args.warmup,
-                                         codes[order[-1]])
+                                         codes[order[-1]], ljac[order[-1]], args.max_newton)
             line["e2e"] = {"value": world * e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                            "d2h_bytes_per_step": d2h}
         if not args.no_cpu_baseline:

@@ -71,6 +71,12 @@ typedef struct {
     double u_e, u_n, u_E;   /* scalings of eq. scalings: erg/g, cm^-3, erg/cm^3               */
     double tau;             /* fraction-to-boundary of the positivity cap (0 < tau < 1)      */
     double lam_min;         /* smallest line-search parameter                                */
+    double growth_max;      /* watchdog line search: a full step may raise ||f|| up to
+                               growth_max times the best ||f|| of the step ...               */
+    int watchdog;           /* ... for at most this many Newton iterations in a row          */
+    int limiter_jacobian;   /* 0: D lagged in the Newton matrix (symmetric S, CG);
+                               1: dD/dE kept and only the opacity lagged, as Sec. 3.2.1
+                               states (non-symmetric S, BiCGStab with the same V-cycle)     */
     int max_newton;         /* Newton iterations per step                                    */
     int max_pcg;            /* CG iterations per Newton iteration                            */
     int guess;              /* RHI_GUESS_*                                                   */
@@ -85,24 +91,28 @@ typedef struct {
     double photon_energy;   /* mean photon energy (erg) used by rhi_set_sources              */
 } rhi_params;
 
+#define RHI_MAX_HISTORY 64
+
 typedef struct {
     int status;             /* RHI_OK or the error of the last step                          */
     int newton_its;         /* Newton iterations of the last step                            */
     int pcg_its;            /* CG iterations summed over the step                            */
     int vcycles;            /* preconditioner applications summed over the step              */
     int backtracks;         /* line-search halvings                                          */
-    int full_steps;         /* line searches that fell back to the full step                 */
+    int lam_min_steps;      /* line searches that ended at lam_min                           */
     int guess_used;         /* RHI_GUESS_* actually used (learned falls back to previous)    */
     int launches;           /* kernel launches of the last step                              */
     double res_initial;     /* ||f(U_0)|| (eq. rmsnorm, scaled)                              */
     double res_final;       /* ||f(U^{n+1})||                                                */
     double res_guess_prev;  /* ||f(U^n)|| when a learned guess was tried, else 0             */
     double ms;              /* device time of the last step, ms                              */
+    double res_history[RHI_MAX_HISTORY];  /* ||f|| after 0, 1, .. Newton iterations      */
 } rhi_stats;
 
 typedef struct rhi_ctx* rhi_handle;
 
-/* Defaults: theta 0.51 (Sec. 3.2), limiter on, tau 0.99, lam_min 1/16, max_newton 50,
+/* Defaults: theta 0.51 (Sec. 3.2), limiter on, tau 0.99, lam_min 1/16, growth_max 1e3,
+   watchdog 3, max_newton 50,
    max_pcg 200, previous-step guess, FP64 multigrid with 6 levels, 2 + 2 sweeps, 16 coarse
    sweeps, omega 0.8, scalings 1, and the grey constants of 13.6 eV monochromatic radiation
    with a 6.3e-18 cm^2 HI cross section.  n_species must be 1 or 3. */
@@ -151,12 +161,14 @@ int rhi_get_stats(rhi_handle h, rhi_stats* out);
 /* The first Newton linear system of a step from the current state with the previous-step
    guess (U_0 = U^n), without solving it: the scaled residual f (n_species + 2 blocks of N:
    e_c, n_1.., E; eq. nonlinear_residual divided by the scalings), the Schur matrix diagonal
-   S_diag (N), its off-diagonal face weights S_face (3 blocks of N: the face between a cell and
-   its -x, -y, -z neighbour, as a positive number; the matrix entry is its negative; 0 on
-   zero-flux boundary faces) and the Schur right-hand side rhs = L M^-1 f_M - f_E (N), all in
-   scaled unknowns.  Any output pointer may be NULL. */
+   S_diag (N), its face entries S_lo (3 blocks of N: the entry coupling a cell to its -x, -y,
+   -z neighbour) and S_hi (3 blocks of N: to its +x, +y, +z neighbour), given as positive
+   numbers (the matrix entries are their negatives; 0 where a face carries no flux), and the
+   Schur right-hand side rhs = L M^-1 f_M - f_E (N), all in scaled unknowns.  With
+   limiter_jacobian = 1 the matrix is the non-symmetric one that keeps dD/dE.  Any output
+   pointer may be NULL. */
 int rhi_linearize(rhi_handle h, double dt, double a, double adot, double* f, double* S_diag,
-                  double* S_face, double* rhs, int on_device);
+                  double* S_lo, double* S_hi, double* rhs, int on_device);
 
 /* Applies the configured preconditioner (one V-cycle or Jacobi) of the Schur matrix built by
    the last rhi_linearize to r (N), writing z (N). */

@@ -19,8 +19,9 @@ Readings of the paper made here (each also listed in the design notes):
   |E_b - E_a| / (a dx (E_a + E_b)/2), floored at 1 / (a L) with L the largest extent of
   the grid; kappa at a face is the mean of the two cells' kappa.  ``limiter = False`` gives
   D = c / (3 max(kappa, kappa_floor)).
-* The Newton matrix lags D entirely (Sec. 3.2.1 lags its n_i dependence; lagging its E
-  dependence too keeps the Schur matrix symmetric, which CG needs).
+* The Newton matrix either lags D entirely (``limiter_jacobian = "lagged"``: the Schur matrix is
+  symmetric, as CG needs) or, as Sec. 3.2.1 states, keeps dD/dE and lags only the opacity
+  (``"E"``: a non-symmetric Schur matrix).
 """
 from dataclasses import dataclass, field
 
@@ -56,6 +57,9 @@ class Problem:
     u_E: float = 1.0
     tau: float = 0.99                  # fraction-to-boundary of the positivity limiter
     lam_min: float = 1.0 / 16.0         # smallest line-search parameter
+    limiter_jacobian: str = "lagged"   # "lagged": D frozen in J; "E": dD/dE kept, kappa lagged
+    growth_max: float = 1e3            # watchdog: a full step may raise ||f|| up to this factor
+    watchdog: int = 3                  # ... for at most this many steps without a new best ||f||
     rates: object = field(default=None)
 
     def __post_init__(self):
@@ -247,6 +251,31 @@ def face_coefficient(p, Ea, Eb, ka, kb, a):
     return D / (a * a * p.dx * p.dx)
 
 
+def face_coefficient_derivatives(p, Ea, Eb, ka, kb, a):
+    """(W, dW/dE_a, dW/dE_b) of ``face_coefficient`` with kappa held fixed (Sec. 3.2.1 lags
+    only the opacity dependence of D).  dD/dR = -c R (4 kappa + R) / (6 kappa^2 + 3 kappa R +
+    R^2)^2 and dR/dE_{a,b} = -/+ sign(E_b - E_a) / (a dx Ebar) - R / (2 Ebar); zero where R
+    sits at its floor or without the limiter."""
+    W = face_coefficient(p, Ea, Eb, ka, kb, a)
+    if not p.limiter:
+        z = np.zeros_like(W)
+        return W, z, z
+    kap = 0.5 * (ka + kb)
+    c = cl.C_LIGHT
+    Ebar = 0.5 * (Ea + Eb)
+    R_min = 1.0 / (a * max(p.nx, p.ny, p.nz) * p.dx)
+    Rraw = np.abs(Eb - Ea) / (a * p.dx * Ebar)
+    live = Rraw > R_min
+    R = np.maximum(Rraw, R_min)
+    den = 6.0 * kap ** 2 + 3.0 * kap * R + R ** 2
+    dDdR = -c * R * (4.0 * kap + R) / den ** 2
+    sgn = np.sign(Eb - Ea)
+    dRa = -sgn / (a * p.dx * Ebar) - R / (2.0 * Ebar)
+    dRb = sgn / (a * p.dx * Ebar) - R / (2.0 * Ebar)
+    f = np.where(live, dDdR / (a * a * p.dx * p.dx), 0.0)
+    return W, f * dRa, f * dRb
+
+
 def face_weights(p, E, kap, a, nbt=None):
     """W[d, cell] for the six faces of every cell (0 on zero-flux boundary faces)."""
     nb, valid = neighbor_table(p) if nbt is None else nbt
@@ -268,14 +297,15 @@ def diffusion_term(p, E, W, nbt=None):
 # --------------------------------------------------------------------------------------------
 # full operator, g^n and residual (eqs. energy/chemistry/radiation_simplified, nonlinear_residual)
 
-def full_operator(p, U, eh, a, adot, T_fixed=None, nbt=None, W=None):
+def full_operator(p, U, eh, a, adot, T_fixed=None, nbt=None, W=None, kap_faces=None):
     """L(U) for every unknown: (L_e, L_n.., D_E + L_E) stacked as (nv, N).  ``W`` freezes the
-    face coefficients (used to check the lagged-D Newton matrix by finite differences)."""
+    face coefficients and ``kap_faces`` only the opacity inside them (used to check the two
+    Newton matrices by finite differences)."""
     ns = p.ns
     ec, n, E = U[0], U[1:1 + ns], U[1 + ns]
     lt = local_terms(p, ec, n, E, eh, p.nH, p.src, a, adot, T_fixed)
     if W is None:
-        W = face_weights(p, E, lt["kappa"], a, nbt)
+        W = face_weights(p, E, lt["kappa"] if kap_faces is None else kap_faces, a, nbt)
     Lfull = np.empty_like(U)
     for v in range(ns + 1):
         Lfull[v] = lt["L"][v]
@@ -307,9 +337,9 @@ def build_g(p, Un, eh, dt, a, adot, T_fixed=None, nbt=None):
     return Un + dt * (p.theta - 1.0) * full_operator(p, Un, eh, a, adot, T_fixed, nbt)
 
 
-def residual(p, U, g, eh, dt, a, adot, T_fixed=None, nbt=None, W=None):
+def residual(p, U, g, eh, dt, a, adot, T_fixed=None, nbt=None, W=None, kap_faces=None):
     """f(U) = U + dt theta L(U) - g^n  (eq. nonlinear_residual)."""
-    return U + dt * p.theta * full_operator(p, U, eh, a, adot, T_fixed, nbt, W) - g
+    return U + dt * p.theta * full_operator(p, U, eh, a, adot, T_fixed, nbt, W, kap_faces) - g
 
 
 def rms_norm(p, f):
@@ -343,14 +373,39 @@ def local_blocks(p, U, eh, dt, a, adot, T_fixed=None):
     return M, Ucol, Lrow, Dloc, lt
 
 
+def diffusion_block(p, E, kap, a, dth, nbt):
+    """The diffusion part of D = I + dt theta J_EE (eq. schur_components) as (diag, rows,
+    cols, vals): with D lagged, face f adds dt theta W_f to the diagonal and -dt theta W_f to
+    the neighbour column; with dD/dE kept (Sec. 3.2.1) the entries of row i are
+    dt theta [W_f + dW_f/dE_i (E_i - E_nb)] and dt theta [-W_f + dW_f/dE_nb (E_i - E_nb)]."""
+    nb, valid = nbt
+    N = p.N
+    cells = np.arange(N)
+    diag = np.zeros(N)
+    rows, cols, vals = [], [], []
+    for d in range(6):
+        m = valid[d]
+        Enb, knb = E[nb[d]], kap[nb[d]]
+        if p.limiter_jacobian == "E":
+            W, dWi, dWn = face_coefficient_derivatives(p, E, Enb, kap, knb, a)
+            dE = E - Enb
+            di = W + dWi * dE
+            off = -W + dWn * dE
+        else:
+            W = face_coefficient(p, E, Enb, kap, knb, a)
+            di, off = W, -W
+        diag += np.where(m, dth * di, 0.0)
+        rows.append(cells[m]); cols.append(nb[d][m]); vals.append(dth * off[m])
+    return diag, rows, cols, vals
+
+
 def full_jacobian(p, U, eh, dt, a, adot, T_fixed=None, nbt=None):
     """The whole scaled Newton matrix (unreduced), sparse, variable-major ordering:
     rows/cols [v * N + cell] for v in (e_c, n_1.., E).  D is lagged (frozen at U)."""
     ns, nm, N = p.ns, p.ns + 1, p.N
     M, Ucol, Lrow, Dloc, lt = local_blocks(p, U, eh, dt, a, adot, T_fixed)
     nbt = neighbor_table(p) if nbt is None else nbt
-    nb, valid = nbt
-    W = face_weights(p, U[1 + ns], lt["kappa"], a, nbt) * (dt * p.theta)
+    ddiag, drows, dcols, dvals = diffusion_block(p, U[1 + ns], lt["kappa"], a, dt * p.theta, nbt)
     cells = np.arange(N)
     rows, cols, vals = [], [], []
     for r in range(nm):
@@ -358,10 +413,9 @@ def full_jacobian(p, U, eh, dt, a, adot, T_fixed=None, nbt=None):
             rows.append(r * N + cells); cols.append(s * N + cells); vals.append(M[:, r, s])
         rows.append(r * N + cells); cols.append(nm * N + cells); vals.append(Ucol[:, r])
         rows.append(nm * N + cells); cols.append(r * N + cells); vals.append(Lrow[:, r])
-    rows.append(nm * N + cells); cols.append(nm * N + cells); vals.append(Dloc + W.sum(axis=0))
-    for d in range(6):
-        m = valid[d]
-        rows.append(nm * N + cells[m]); cols.append(nm * N + nb[d][m]); vals.append(-W[d][m])
+    rows.append(nm * N + cells); cols.append(nm * N + cells); vals.append(Dloc + ddiag)
+    for rr, cc, vv in zip(drows, dcols, dvals):
+        rows.append(nm * N + rr); cols.append(nm * N + cc); vals.append(vv)
     J = sparse.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                           shape=(p.nv * N, p.nv * N))
     return J.tocsr()

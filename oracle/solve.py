@@ -12,17 +12,24 @@ algorithm below eq. nonlinear_residual) with one of three exact linear solves pe
                   (step (i), eq. step_ia), the scalar system S = D - L M^-1 U solved by
                   sparse LU (step (ii)), recovery s_M = -f~_M - M^-1 U s_E (step (iii));
   "schur_cg"      as above with S solved by plain, unpreconditioned conjugate gradients to a
-                  relative residual of 1e-14.
+                  relative residual of 1e-14 (BiCGStab when the Newton matrix keeps dD/dE,
+                  which makes S non-symmetric).
 
 Readings (also listed in the design notes):
-* line search (Sec. 3.2, item 2 of the Newton algorithm): lambda starts at 1 and is halved
-  while ||f(U + lambda S)|| > (1 - 1e-4 lambda) ||f(U)||, down to lam_min = 1/16; when no
-  lambda >= lam_min gives that decrease the full step is taken (with D lagged the iteration
-  is not monotone in ||f|| where radiation free-streams, and tiny steps would stall it);
+* line search (Sec. 3.2, item 2 of the Newton algorithm): a watchdog.  The full (capped) step
+  is taken when it gives a new best ||f|| (by the factor 1 - 1e-4), and also when it does not,
+  for at most ``watchdog`` (3) steps in a row and as long as ||f|| stays below growth_max (1e3)
+  times the best; otherwise lambda is halved from 1 while ||f(U + lambda S)|| > (1 - 1e-4
+  lambda) ||f(U)||, down to lam_min = 1/16 (that last step is taken).  Near bright sources the
+  first Newton steps of a time step raise ||f|| before it falls quadratically: a plain Armijo
+  test there accepted lambda = 1/16 steps that cut ||f|| by a few percent per iteration (18
+  iterations instead of 5 on sub-boxes of the 256^3 recipe), while purely non-monotone full
+  steps can cycle across the kinks of the tabulated rates;
 * positivity: before the line search each cell's step is capped so that e, E and every
-  species density (independent and derived) keep at least (1 - tau) of their current value
-  (fraction to the boundary, tau = 0.99); the cap multiplies the whole cell vector; species
-  decreases smaller than 1e-13 of the element total are roundoff and do not bind;
+  species density (independent and derived) keep at least (1 - tau) of their current
+  distance to their bound (fraction to the boundary, tau = 0.99); the cap multiplies the whole
+  cell vector; e and E are bounded by 0, species by -1e-13 of their element total (a species
+  at zero may then still move by roundoff instead of freezing its cell);
 * explicit predictor (eq. explicit_predictor): the paper prints U^n + dt L^n; since L is
   defined with dU/dt = -L (eqs. mLe, mLn, mLE), the explicit Euler step is U^n - dt L(U^n);
   it is capped the same way as a Newton step.
@@ -40,8 +47,8 @@ from . import model as md
 
 def _cell_quantities(p, U, eh):
     """Quantities that must stay positive, e, E and all species (independent and derived),
-    each with the size of a change below which a decrease is roundoff: 0 for e and E, and
-    1e-13 of the element total for the species."""
+    each with its roundoff allowance below zero: 0 for e and E, 1e-13 of the element total for
+    the species."""
     ns = p.ns
     nHI, nHeI, nHeII = p.species_full(U[1:1 + ns])
     nHe = p.y_he * p.nH
@@ -62,13 +69,15 @@ def _quantity_changes(p, S):
 
 
 def step_caps(p, U, eh, S):
-    """Largest fraction <= 1 of the step S per cell that keeps every bounded quantity above
-    (1 - tau) times its current value; decreases within roundoff of a species' element total
-    do not bind (a species at exactly zero would otherwise freeze its cell)."""
+    """Largest fraction <= 1 of the step S per cell that keeps every bounded quantity q above
+    its bound -tiny by at least (1 - tau) of its current distance q + tiny (fraction to the
+    boundary).  tiny = 0 for e and E; for a species it is 1e-13 of its element total, so a
+    species at or near zero can still move by roundoff-sized amounts instead of freezing its
+    cell."""
     cap = np.ones(p.N)
     for (q, tiny), dq in zip(_cell_quantities(p, U, eh), _quantity_changes(p, S)):
-        binds = dq < -tiny
-        frac = np.where(binds, p.tau * q / np.where(binds, -dq, 1.0), 1.0)
+        neg = dq < 0.0
+        frac = np.where(neg, p.tau * (q + tiny) / np.where(neg, -dq, 1.0), 1.0)
         cap = np.minimum(cap, np.maximum(frac, 0.0))
     return cap
 
@@ -98,6 +107,38 @@ def cg(A, b, rtol=1e-14, maxiter=20000):
     return x, its
 
 
+def bicgstab(A, b, rtol=1e-14, maxiter=20000):
+    """Plain (unpreconditioned) BiCGStab, x0 = 0; stops at ||r||_2 <= rtol ||b||_2."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    rh = r.copy()
+    rho = alpha = omega = 1.0
+    v = np.zeros_like(b)
+    p_ = np.zeros_like(b)
+    stop = rtol * np.sqrt(b @ b)
+    its = 0
+    while np.sqrt(r @ r) > stop and its < maxiter:
+        rho_new = rh @ r
+        beta = (rho_new / rho) * (alpha / omega)
+        p_ = r + beta * (p_ - omega * v)
+        v = A @ p_
+        alpha = rho_new / (rh @ v)
+        s = r - alpha * v
+        its += 1
+        if np.sqrt(s @ s) <= stop:
+            x += alpha * p_
+            r = s
+            break
+        t = A @ s
+        omega = (t @ s) / (t @ t)
+        x += alpha * p_ + omega * s
+        r = s - omega * t
+        rho = rho_new
+    if np.sqrt(r @ r) > stop:
+        raise RuntimeError("oracle BiCGStab did not converge")
+    return x, its
+
+
 def schur_system(p, U, f, eh, dt, a, adot, T_fixed=None, nbt=None):
     """Steps (i) and (ii) setup of Sec. 3.2.1 in scaled unknowns.
 
@@ -114,14 +155,11 @@ def schur_system(p, U, f, eh, dt, a, adot, T_fixed=None, nbt=None):
     MiU = np.linalg.solve(M, Ucol[:, :, None])[:, :, 0]       #           M (M^-1 U) = U
     dS = Dloc - np.einsum("ij,ij->i", Lrow, MiU)
     rhs = np.einsum("ij,ij->i", Lrow, fM_t) - fE
-    W = md.face_weights(p, U[nm], lt["kappa"], a, nbt) * (dt * p.theta)
+    ddiag, drows, dcols, dvals = md.diffusion_block(p, U[nm], lt["kappa"], a, dt * p.theta, nbt)
     cells = np.arange(N)
-    rows = [cells]
-    cols = [cells]
-    vals = [dS + W.sum(axis=0)]
-    for d in range(6):
-        m = valid[d]
-        rows.append(cells[m]); cols.append(nb[d][m]); vals.append(-W[d][m])
+    rows = [cells] + drows
+    cols = [cells] + dcols
+    vals = [dS + ddiag] + dvals
     S = sparse.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                           shape=(N, N)).tocsr()
     return S, rhs, fM_t, MiU
@@ -142,7 +180,7 @@ def newton_direction(p, U, f, eh, dt, a, adot, T_fixed=None, nbt=None, linear="d
         sE = spla.spsolve(S.tocsc(), rhs)
         its = 0
     elif linear == "schur_cg":
-        sE, its = cg(S, rhs)
+        sE, its = cg(S, rhs) if p.limiter_jacobian == "lagged" else bicgstab(S, rhs)
     else:
         raise ValueError(linear)
     sM = -fM_t - MiU * sE[:, None]                             # step (iii)
@@ -163,28 +201,35 @@ def newton(p, U0, g, eh, dt, a, adot, tol, T_fixed=None, linear="direct", max_ne
     r = md.rms_norm(p, f)
     stats = dict(newton_its=0, linear_its=0, backtracks=0, full_step_fallbacks=0,
                  res_history=[r], converged=False)
+    r_best, bad = r, 0
     for _ in range(max_newton):
         if r < tol:
             break
         S, its = newton_direction(p, U, f, eh, dt, a, adot, T_fixed, nbt, linear)
         stats["linear_its"] += its
         cap = step_caps(p, U, eh, S)
-        lam = 1.0
-        while True:
+
+        def trial(lam):
             Ut = U + np.minimum(lam, cap)[None, :] * S
             ft = md.residual(p, Ut, g, eh, dt, a, adot, T_fixed, nbt)
-            rt = md.rms_norm(p, ft)
-            if rt <= (1.0 - 1e-4 * lam) * r:
-                break
-            if lam * 0.5 < p.lam_min:
-                # no sufficient decrease down to lam_min: take the full (capped) step
-                Ut = U + cap[None, :] * S
-                ft = md.residual(p, Ut, g, eh, dt, a, adot, T_fixed, nbt)
-                rt = md.rms_norm(p, ft)
-                stats["full_step_fallbacks"] += 1
-                break
-            lam *= 0.5
-            stats["backtracks"] += 1
+            return Ut, ft, md.rms_norm(p, ft)
+
+        Ut, ft, rt = trial(1.0)
+        if rt <= (1.0 - 1e-4) * r_best:            # a new best residual
+            r_best, bad = rt, 0
+        elif bad < p.watchdog and rt <= p.growth_max * r_best:
+            bad += 1                               # tolerated non-monotone full step
+        else:                                      # Armijo backtracking from U
+            lam = 1.0
+            while not rt <= (1.0 - 1e-4 * lam) * r:
+                if lam * 0.5 < p.lam_min:
+                    stats["full_step_fallbacks"] += 1
+                    break
+                lam *= 0.5
+                stats["backtracks"] += 1
+                Ut, ft, rt = trial(lam)
+            bad = 0
+            r_best = min(r_best, rt)
         U, f, r = Ut, ft, rt
         stats["newton_its"] += 1
         stats["res_history"].append(r)

@@ -33,6 +33,7 @@ class rhi_params(C.Structure):
                 ("m_grey", C.c_int), ("isothermal", C.c_int), ("limiter", C.c_int),
                 ("kappa_floor", C.c_double), ("u_e", C.c_double), ("u_n", C.c_double),
                 ("u_E", C.c_double), ("tau", C.c_double), ("lam_min", C.c_double),
+                ("growth_max", C.c_double), ("watchdog", C.c_int), ("limiter_jacobian", C.c_int),
                 ("max_newton", C.c_int), ("max_pcg", C.c_int), ("guess", C.c_int),
                 ("precond", C.c_int), ("mg_levels", C.c_int), ("mg_pre", C.c_int),
                 ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double),
@@ -42,9 +43,10 @@ class rhi_params(C.Structure):
 
 class rhi_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("newton_its", C.c_int), ("pcg_its", C.c_int),
-                ("vcycles", C.c_int), ("backtracks", C.c_int), ("full_steps", C.c_int),
+                ("vcycles", C.c_int), ("backtracks", C.c_int), ("lam_min_steps", C.c_int),
                 ("guess_used", C.c_int), ("launches", C.c_int), ("res_initial", C.c_double),
-                ("res_final", C.c_double), ("res_guess_prev", C.c_double), ("ms", C.c_double)]
+                ("res_final", C.c_double), ("res_guess_prev", C.c_double), ("ms", C.c_double),
+                ("res_history", C.c_double * 64)]
 
 
 _P = C.c_void_p
@@ -60,7 +62,8 @@ _SIGS = {
                                     C.c_double]),
     "rhi_get_state": (C.c_int, [_P, _P, _P, _P, C.c_int]),
     "rhi_get_stats": (C.c_int, [_P, C.POINTER(rhi_stats)]),
-    "rhi_linearize": (C.c_int, [_P, C.c_double, C.c_double, C.c_double, _P, _P, _P, _P, C.c_int]),
+    "rhi_linearize": (C.c_int, [_P, C.c_double, C.c_double, C.c_double, _P, _P, _P, _P, _P,
+                                C.c_int]),
     "rhi_precond_apply": (C.c_int, [_P, _P, _P, C.c_int]),
     "rhi_set_profiling": (C.c_int, [_P, C.c_int]),
     "rhi_kernel_times": (C.c_int, [_P, C.c_int, C.c_char_p, _D, C.POINTER(C.c_int)]),
@@ -208,17 +211,22 @@ class Solver:
     def stats(self):
         s = rhi_stats()
         lib().rhi_get_stats(self.h, C.byref(s))
-        return {k: getattr(s, k) for k, _ in rhi_stats._fields_}
+        out = {k: getattr(s, k) for k, _ in rhi_stats._fields_ if k != "res_history"}
+        out["res_history"] = list(s.res_history[:min(s.newton_its + 1, 64)])
+        return out
 
     def linearize(self, dt, a=1.0, adot=0.0):
         nv = self.ns + 2
         f = np.empty(nv * self.N)
         d = np.empty(self.N)
-        fc = np.empty(3 * self.N)
+        lo = np.empty(3 * self.N)
+        hi = np.empty(3 * self.N)
         r = np.empty(self.N)
         self._check(lib().rhi_linearize(self.h, dt, a, adot, f.ctypes.data, d.ctypes.data,
-                                        fc.ctypes.data, r.ctypes.data, 0), "rhi_linearize")
-        return dict(f=f.reshape(nv, self.N), diag=d, face=fc.reshape(3, self.N), rhs=r)
+                                        lo.ctypes.data, hi.ctypes.data, r.ctypes.data, 0),
+                    "rhi_linearize")
+        return dict(f=f.reshape(nv, self.N), diag=d, face=lo.reshape(3, self.N),
+                    face_hi=hi.reshape(3, self.N), rhs=r)
 
     def precond_apply(self, r):
         r = np.ascontiguousarray(r, dtype=np.float64)

@@ -103,12 +103,16 @@ struct rhi_ctx {
     double* U[2] = {nullptr, nullptr};
     double* kap[2] = {nullptr, nullptr};
     double* W[2] = {nullptr, nullptr};
+    double* PQ[2] = {nullptr, nullptr};         // Newton-matrix face entries (dD/dE kept)
+    double* diag_ns[2] = {nullptr, nullptr};
     double* g = nullptr;
     double *diag[2] = {nullptr, nullptr}, *rhs[2] = {nullptr, nullptr};
     double *fMt[2] = {nullptr, nullptr}, *MiU[2] = {nullptr, nullptr};
     double* f_tmp = nullptr;
     // CG
     double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+    // BiCGStab
+    double *rh = nullptr, *v = nullptr, *s = nullptr, *t = nullptr, *ph = nullptr, *sh = nullptr;
     double* partials = nullptr;
     double* scal = nullptr;
     double* h_scal = nullptr;   // pinned
@@ -117,8 +121,9 @@ struct rhi_ctx {
     // multigrid
     std::vector<Level<double>> mg64;
     std::vector<Level<float>> mg32;
-    // operator the preconditioner was set up for
+    // operator the preconditioner was set up for, and the Newton matrix when dD/dE is kept
     Op<double> op0{};
+    OpNS opns{};
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -162,6 +167,7 @@ StepParams make_params(const rhi_ctx* h, double dt, double a, double adot) {
     P.kappa_floor = h->prm.kappa_floor;
     P.m_grey = (double)h->prm.m_grey;
     P.isothermal = h->prm.isothermal; P.limiter = h->prm.limiter;
+    P.limiter_newton = h->prm.limiter_jacobian;
     P.y_he = h->prm.y_he;
     P.u_e = h->prm.u_e; P.u_n = h->prm.u_n; P.u_E = h->prm.u_E;
     P.iu_e = 1.0 / P.u_e; P.iu_n = 1.0 / P.u_n; P.iu_E = 1.0 / P.u_E;
@@ -381,6 +387,56 @@ int pcg(rhi_ctx* h, const double* rhs, double tol, int* its_out) {
     return RHI_OK;
 }
 
+// Right-preconditioned BiCGStab on the non-symmetric Schur matrix h->opns (dD/dE kept), with
+// the symmetric lagged-D V-cycle as preconditioner; stops at ||r||_RMS <= tol; solution in h->x.
+int bicgstab(rhi_ctx* h, const double* rhs, double tol, int* its_out) {
+    LinLaunch L(h->st, &h->prof);
+    const long long N = h->N;
+    const double norm = 1.0 / ((double)N * h->nv);
+    int np = 0;
+    CK(L.bicg_init(N, rhs, h->r, h->rh, h->x, h->partials, np));
+    CK(L.reduce(h->partials, np, h->scal, RED_SUM, S_RR));
+    double rr;
+    int rc = read_scalar(h, S_RR, &rr);
+    if (rc) return rc;
+    h->h_scal[S_RHO] = rr;     // rho_0 = rh.r = r.r
+    CK(cudaMemcpyAsync(h->scal + S_RHO, &h->h_scal[S_RHO], sizeof(double), cudaMemcpyHostToDevice, h->st));
+    int its = 0;
+    if (std::sqrt(rr * norm) > tol) {
+        for (its = 1; its <= h->prm.max_pcg; ++its) {
+            CK(L.bicg_p(N, h->scal, h->r, h->v, h->p, its == 1));
+            double* z = nullptr;
+            if ((rc = precond_apply(h, h->p, &z, np))) return rc;
+            std::swap(h->ph, h->z);                              // ph = M^-1 p
+            CK(L.matvec_ns(h->opns, h->ph, h->v, h->rh, 0, h->partials, np));
+            CK(L.reduce(h->partials, np, h->scal, RED_BICG_ALPHA, 0));
+            CK(L.bicg_s(N, h->scal, h->r, h->v, h->s, h->partials, np));
+            CK(L.reduce(h->partials, np, h->scal, RED_SUM, S_SS));
+            double ss;
+            if ((rc = read_scalar(h, S_SS, &ss))) return rc;
+            if (h->h_scal[S_BREAK] != 0.0 || !std::isfinite(ss))
+                return fail(h, RHI_ERR_NONPHYSICAL, "BiCGStab breakdown");
+            if (std::sqrt(ss * norm) <= tol) {                  // x += alpha ph
+                CK(L.axpy(N, h->scal, S_ALPHA, h->ph, h->x));
+                break;
+            }
+            if ((rc = precond_apply(h, h->s, &z, np))) return rc;
+            std::swap(h->sh, h->z);                              // sh = M^-1 s
+            CK(L.matvec_ns(h->opns, h->sh, h->t, h->s, 1, h->partials, np));
+            CK(L.reduce(h->partials, np, h->scal, RED_BICG_OMEGA, 0));
+            CK(L.bicg_xr(N, h->scal, h->x, h->ph, h->sh, h->s, h->t, h->r, h->rh, h->partials, np));
+            CK(L.reduce(h->partials, np, h->scal, RED_BICG_RHO, 0));
+            if ((rc = read_scalar(h, S_RR, &rr))) return rc;
+            if (h->h_scal[S_BREAK] != 0.0 || !std::isfinite(rr))
+                return fail(h, RHI_ERR_NONPHYSICAL, "BiCGStab breakdown");
+            if (std::sqrt(rr * norm) <= tol) break;
+        }
+        if (its > h->prm.max_pcg) its = h->prm.max_pcg;
+    }
+    *its_out = its;
+    return RHI_OK;
+}
+
 // ---------------------------------------------------------------------------------------------
 // the physics launches, bracketed for the profiler
 
@@ -401,9 +457,10 @@ int cell(rhi_ctx* h, const StepParams& P, int mode, PhysBuffers B) {
 }
 int ncell_blocks(const rhi_ctx* h) { return (int)((h->N + cell_block_size() - 1) / cell_block_size()); }
 
-int faces(rhi_ctx* h, const StepParams& P, const double* E, const double* kap, double* W) {
+int faces(rhi_ctx* h, const StepParams& P, const double* E, const double* kap, double* W,
+          double* PQ) {
     Scope s(h->prof, "faces_limiter");
-    CK(launch_faces(P, E, kap, W, h->st));
+    CK(launch_faces(P, E, kap, W, PQ, h->st));
     return RHI_OK;
 }
 int kappa(rhi_ctx* h, const StepParams& P, const double* n, double* kap) {
@@ -420,6 +477,18 @@ void set_op0(rhi_ctx* h, const StepParams& P, int set, const double* W) {
     A.scale = P.dth;
 }
 
+void set_opns(rhi_ctx* h, const StepParams& P, int set, const double* PQ) {
+    OpNS& A = h->opns;
+    A.nx = h->grid.nx; A.ny = h->grid.ny; A.nz = h->grid.nz; A.N = h->N;
+    for (int a = 0; a < 3; ++a) {
+        A.per[a] = h->per[a];
+        A.P[a] = PQ + a * h->N;
+        A.Q[a] = PQ + (3 + a) * h->N;
+    }
+    A.diag = h->diag_ns[set];
+    A.scale = P.dth;
+}
+
 // U views of a work buffer
 double* U_ec(rhi_ctx* h, int b) { return h->U[b]; }
 double* U_n(rhi_ctx* h, int b) { return h->U[b] + h->N; }
@@ -433,10 +502,12 @@ int validate_params(const rhi_params* p) {
     if (!(p->u_e > 0.0 && p->u_n > 0.0 && p->u_E > 0.0)) return 0;
     if (!(p->tau > 0.0 && p->tau < 1.0)) return 0;
     if (!(p->lam_min > 0.0 && p->lam_min <= 1.0)) return 0;
+    if (!(p->growth_max >= 1.0) || p->watchdog < 0) return 0;
     if (p->max_newton < 0 || p->max_pcg < 1) return 0;
     if (p->guess < 0 || p->guess > RHI_GUESS_PREDICTOR) return 0;
     if (p->precond < 0 || p->precond > RHI_PRECOND_MG_FP32) return 0;
     if (p->mg_levels < 1 || p->mg_pre < 1 || p->mg_post < 0 || p->mg_coarse_sweeps < 1) return 0;
+    if (p->limiter_jacobian != 0 && p->limiter_jacobian != 1) return 0;
     if (!(p->mg_omega > 0.0 && p->mg_omega <= 1.0)) return 0;
     return 1;
 }
@@ -461,6 +532,9 @@ int rhi_params_default(rhi_params* p, int n_species) {
     p->u_e = p->u_n = p->u_E = 1.0;
     p->tau = 0.99;
     p->lam_min = 1.0 / 16.0;
+    p->growth_max = 1e3;
+    p->watchdog = 3;
+    p->limiter_jacobian = 0;
     p->max_newton = 50;
     p->max_pcg = 200;
     p->guess = RHI_GUESS_PREVIOUS;
@@ -509,11 +583,15 @@ int rhi_create(const rhi_grid* grid, const rhi_bc* bc, const rhi_params* params,
         A(&h->U[b], (size_t)h->nv * N); A(&h->kap[b], N); A(&h->W[b], 3 * (size_t)N);
         A(&h->diag[b], N); A(&h->rhs[b], N); A(&h->fMt[b], (size_t)h->nm * N);
         A(&h->MiU[b], (size_t)h->nm * N);
+        if (params->limiter_jacobian) { A(&h->PQ[b], 6 * (size_t)N); A(&h->diag_ns[b], N); }
+    }
+    if (params->limiter_jacobian) {
+        A(&h->rh, N); A(&h->v, N); A(&h->s, N); A(&h->t, N); A(&h->ph, N); A(&h->sh, N);
     }
     A(&h->g, (size_t)h->nv * N);
     A(&h->x, N); A(&h->r, N); A(&h->z, N); A(&h->p, N); A(&h->q, N);
     const long long nparts = std::max<long long>((N + cell_block_size() - 1) / cell_block_size(),
-                                                 stream_blocks(N));
+                                                 2 * (long long)stream_blocks(N));
     A(&h->partials, (size_t)nparts);
     A(&h->scal, S_NSCAL);
     if (!rc) rc = dalloc(h, &h->d_flag, 1);
@@ -664,35 +742,44 @@ int rhi_kernel_times(rhi_handle h, int max, char* names, double* total_ms, int* 
 }
 
 int rhi_linearize(rhi_handle h, double dt, double a, double adot, double* f, double* S_diag,
-                  double* S_face, double* rhs, int on_device) {
+                  double* S_lo, double* S_hi, double* rhs, int on_device) {
     if (!h) return RHI_ERR_ARG;
     if (!h->have_state) return fail(h, RHI_ERR_STATE, "rhi_linearize: no state");
     if (!(dt > 0.0) || !(a > 0.0)) return fail(h, RHI_ERR_ARG, "rhi_linearize: dt > 0 and a > 0 required");
     const StepParams P = make_params(h, dt, a, adot);
     int rc;
     if ((rc = kappa(h, P, h->n_s, h->kap[0]))) return rc;
-    if ((rc = faces(h, P, h->E_s, h->kap[0], h->W[0]))) return rc;
+    if ((rc = faces(h, P, h->E_s, h->kap[0], h->W[0], h->PQ[0]))) return rc;
     PhysBuffers B = state_buffers(h);
     B.W = h->W[0];
+    B.PQ = h->PQ[0]; B.diag_ns = h->diag_ns[0];
     B.diag = h->diag[0]; B.rhs = h->rhs[0]; B.fMt = h->fMt[0]; B.MiU = h->MiU[0];
-    // residual: straight into a device destination, or via a free work buffer for the host
+    // the residual goes straight to a device destination, or via a free work buffer
     if (f) B.f_out = on_device ? f : h->U[1];
     if ((rc = cell(h, P, MODE_PREP, B))) return rc;
     set_op0(h, P, 0, h->W[0]);
+    if (h->prm.limiter_jacobian) set_opns(h, P, 0, h->PQ[0]);
     if ((rc = precond_setup(h))) return rc;
     const long long N = h->N;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (f && !on_device) CK(cudaMemcpyAsync(f, h->U[1], (size_t)h->nv * N * sizeof(double), kind, h->st));
-    if (S_diag) CK(cudaMemcpyAsync(S_diag, h->diag[0], N * sizeof(double), kind, h->st));
+    const double* dsrc = h->prm.limiter_jacobian ? h->diag_ns[0] : h->diag[0];
+    if (S_diag) CK(cudaMemcpyAsync(S_diag, dsrc, N * sizeof(double), kind, h->st));
     if (rhs) CK(cudaMemcpyAsync(rhs, h->rhs[0], N * sizeof(double), kind, h->st));
-    if (S_face) {
-        // S_face = dt theta W (scaled on the host; a test and inspection path)
-        std::vector<double> tmp(3 * (size_t)N);
-        CK(cudaMemcpyAsync(tmp.data(), h->W[0], 3 * N * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-        CK(cudaStreamSynchronize(h->st));
-        for (auto& v : tmp) v *= P.dth;
-        if (on_device) CK(cudaMemcpy(S_face, tmp.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice));
-        else std::memcpy(S_face, tmp.data(), 3 * N * sizeof(double));
+    if (S_lo || S_hi) {
+        // face entries of the Newton matrix (an inspection path: a temporary buffer)
+        double* tmp = nullptr;
+        CK(cudaMalloc(&tmp, 6 * N * sizeof(double)));
+        cudaError_t e = cudaSuccess;
+        {
+            Scope s(h->prof, "export_faces");
+            e = launch_export_faces(P, h->W[0], h->PQ[0], tmp, tmp + 3 * N, h->st);
+        }
+        if (e == cudaSuccess && S_lo) e = cudaMemcpyAsync(S_lo, tmp, 3 * N * sizeof(double), kind, h->st);
+        if (e == cudaSuccess && S_hi) e = cudaMemcpyAsync(S_hi, tmp + 3 * N, 3 * N * sizeof(double), kind, h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        cudaFree(tmp);
+        if (e != cudaSuccess) return fail(h, RHI_ERR_CUDA, std::string("rhi_linearize: ") + cudaGetErrorString(e));
     }
     CK(cudaStreamSynchronize(h->st));
     h->prof.resolve();
@@ -735,9 +822,10 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
 
     // ---- g^n and the initial iterate U_0
     if ((rc = kappa(h, P, h->n_s, h->kap[0]))) return rc;
-    if ((rc = faces(h, P, h->E_s, h->kap[0], h->W[0]))) return rc;
+    if ((rc = faces(h, P, h->E_s, h->kap[0], h->W[0], h->PQ[0]))) return rc;
     PhysBuffers B = state_buffers(h);
     B.W = h->W[0];
+    B.PQ = h->PQ[0]; B.diag_ns = h->diag_ns[0];
     int cur = -1;            // -1: U_k is the state U^n (e_c = 0); 0 / 1: work buffer
     int set = 0;             // Schur set of U_k
     double res = 0.0;
@@ -750,9 +838,10 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
         if ((rc = cell(h, P, MODE_PREP_PREDICT, B))) return rc;
         cur = 0;
         if ((rc = kappa(h, P, U_n(h, 0), h->kap[0]))) return rc;
-        if ((rc = faces(h, P, U_E(h, 0), h->kap[0], h->W[0]))) return rc;
+        if ((rc = faces(h, P, U_E(h, 0), h->kap[0], h->W[0], h->PQ[0]))) return rc;
         PhysBuffers C = state_buffers(h);
         C.ec = U_ec(h, 0); C.n = U_n(h, 0); C.E = U_E(h, 0); C.W = h->W[0];
+        C.PQ = h->PQ[0]; C.diag_ns = h->diag_ns[0];
         C.diag = h->diag[0]; C.rhs = h->rhs[0]; C.fMt = h->fMt[0]; C.MiU = h->MiU[0];
         if ((rc = cell(h, P, MODE_ITER, C))) return rc;
         if ((rc = residual_norm(h, ncell_blocks(h), &res))) return rc;
@@ -763,41 +852,68 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
 
     // ---- Newton iteration
     int k = 0;
+    double r_best = res;
+    int bad = 0;
+    S.res_history[0] = res;
     while (!(res < newton_tol) && k < h->prm.max_newton) {
         const double* Wk = h->W[cur < 0 ? 0 : cur];
         set_op0(h, P, set, Wk);
         if ((rc = precond_setup(h))) return rc;
         int its = 0;
-        if ((rc = pcg(h, h->rhs[set], lin_tol * res, &its))) { S.status = rc; return rc; }
+        if (h->prm.limiter_jacobian) {
+            set_opns(h, P, set, h->PQ[cur < 0 ? 0 : cur]);
+            if ((rc = bicgstab(h, h->rhs[set], lin_tol * res, &its))) { S.status = rc; return rc; }
+        } else if ((rc = pcg(h, h->rhs[set], lin_tol * res, &its))) {
+            S.status = rc;
+            return rc;
+        }
         S.pcg_its += its;
         const int t = (cur == 0) ? 1 : 0;
         const double* ec0 = cur < 0 ? nullptr : U_ec(h, cur);
         const double* n0 = cur < 0 ? h->n_s : U_n(h, cur);
         const double* E0 = cur < 0 ? h->E_s : U_E(h, cur);
-        double lam = 1.0, rt = 0.0;
-        bool fallback = false;
-        while (true) {
+        // U_k + min(lam, cap) S_k into buffer t, its faces, residual and Schur set
+        auto trial = [&](double lam, double* rt) -> int {
             {
                 Scope s(h->prof, "update_recover_limit");
                 CK(launch_update(P, ns, lam, ec0, n0, E0, h->e_s, h->nH, h->x, h->fMt[set],
                                  h->MiU[set], U_ec(h, t), U_n(h, t), U_E(h, t), h->kap[t], h->st));
             }
-            if ((rc = faces(h, P, U_E(h, t), h->kap[t], h->W[t]))) return rc;
+            int r2;
+            if ((r2 = faces(h, P, U_E(h, t), h->kap[t], h->W[t], h->PQ[t]))) return r2;
             PhysBuffers C = state_buffers(h);
             C.ec = U_ec(h, t); C.n = U_n(h, t); C.E = U_E(h, t); C.W = h->W[t];
+            C.PQ = h->PQ[t]; C.diag_ns = h->diag_ns[1 - set];
             C.diag = h->diag[1 - set]; C.rhs = h->rhs[1 - set];
             C.fMt = h->fMt[1 - set]; C.MiU = h->MiU[1 - set];
-            if ((rc = cell(h, P, MODE_ITER, C))) return rc;
-            if ((rc = residual_norm(h, ncell_blocks(h), &rt))) return rc;
-            if (fallback || rt <= (1.0 - 1e-4 * lam) * res) break;
-            if (lam * 0.5 < h->prm.lam_min) { lam = 1.0; fallback = true; S.full_steps += 1; continue; }
-            lam *= 0.5;
-            S.backtracks += 1;
+            if ((r2 = cell(h, P, MODE_ITER, C))) return r2;
+            return residual_norm(h, ncell_blocks(h), rt);
+        };
+        // watchdog line search (Sec. 3.2, item 2): full steps, non-monotone for at most
+        // `watchdog` iterations without a new best ||f||, else Armijo backtracking
+        double rt = 0.0;
+        if ((rc = trial(1.0, &rt))) return rc;
+        if (rt <= (1.0 - 1e-4) * r_best) {
+            r_best = rt;
+            bad = 0;
+        } else if (bad < h->prm.watchdog && rt <= h->prm.growth_max * r_best) {
+            bad += 1;
+        } else {
+            double lam = 1.0;
+            while (!(rt <= (1.0 - 1e-4 * lam) * res)) {
+                if (lam * 0.5 < h->prm.lam_min) { S.lam_min_steps += 1; break; }
+                lam *= 0.5;
+                S.backtracks += 1;
+                if ((rc = trial(lam, &rt))) return rc;
+            }
+            bad = 0;
+            r_best = std::min(r_best, rt);
         }
         cur = t;
         set = 1 - set;
         res = rt;
         ++k;
+        if (k < RHI_MAX_HISTORY) S.res_history[k] = res;
         if (!std::isfinite(res)) break;
     }
     S.newton_its = k;

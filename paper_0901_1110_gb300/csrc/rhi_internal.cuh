@@ -50,6 +50,7 @@ struct StepParams {
     double kappa_floor;
     double m_grey;
     int isothermal, limiter;
+    int limiter_newton;               // 1: keep dD/dE in the Newton matrix (non-symmetric S)
     double y_he;
     double u_e, u_n, u_E, iu_e, iu_n, iu_E;
     double sk[3], pg[3], ph[3];
@@ -129,9 +130,11 @@ struct PhysBuffers {
     const double* E;
     const double* kap;
     const double* W;        // 3 * N lower-face coefficients (per unit time)
+    const double* PQ;       // 6 * N Newton-matrix face entries (P then Q) or null
     double* g;              // (ns + 2) * N
     // outputs of the cell kernel
-    double* diag;           // Schur diagonal (scaled)
+    double* diag;           // Schur diagonal with D lagged (scaled; the preconditioner's)
+    double* diag_ns;        // Schur diagonal with dD/dE kept (when PQ is given)
     double* rhs;            // Schur right-hand side (scaled)
     double* fMt;            // (ns + 1) * N   M^-1 f_M (scaled)
     double* MiU;            // (ns + 1) * N   M^-1 U  (scaled)
@@ -145,7 +148,9 @@ enum CellMode { MODE_PREP = 0, MODE_ITER = 1, MODE_PREP_PREDICT = 2 };
 cudaError_t launch_kappa(const StepParams& P, int ns, const double* n, double* kap,
                          cudaStream_t st);
 cudaError_t launch_faces(const StepParams& P, const double* E, const double* kap, double* W,
-                         cudaStream_t st);
+                         double* PQ, cudaStream_t st);
+cudaError_t launch_export_faces(const StepParams& P, const double* W, const double* PQ,
+                                double* S_lo, double* S_hi, cudaStream_t st);
 cudaError_t launch_cell(const StepParams& P, int ns, int mode, const PhysBuffers& B,
                         int nblocks, cudaStream_t st);
 int cell_block_size();

@@ -166,11 +166,155 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce(const double* __restrict__
             scal[S_PQ] = s;
             if (!(s > 0.0)) scal[S_BREAK] = 1.0;
             scal[S_ALPHA] = (s > 0.0) ? scal[S_RZ] / s : 0.0;
-        } else {
+        } else if (op == RED_BETA) {
             scal[S_BETA] = s / scal[S_RZ];
             scal[S_RZ] = s;
+        } else if (op == RED_BICG_ALPHA) {          // s = rh.v
+            scal[S_RV] = s;
+            if (!(s != 0.0)) scal[S_BREAK] = 1.0;
+            scal[S_ALPHA] = (s != 0.0) ? scal[S_RHO] / s : 0.0;
+        } else if (op == RED_BICG_OMEGA) {          // partials: t.s then t.t
+            double tt = 0.0;
+            for (int q = 0; q < n; ++q) tt += partials[n + q];
+            scal[S_TS] = s;
+            scal[S_TT] = tt;
+            scal[S_OMEGA] = (tt > 0.0) ? s / tt : 0.0;
+            if (!(tt > 0.0)) scal[S_BREAK] = 1.0;
+        } else {                                    // RED_BICG_RHO: partials r.r then rh.r
+            double rho = 0.0;
+            for (int q = 0; q < n; ++q) rho += partials[n + q];
+            scal[S_RR] = s;
+            scal[S_BETA] = (rho / scal[S_RHO]) * (scal[S_ALPHA] / scal[S_OMEGA]);
+            scal[S_RHO] = rho;
+            if (!(rho != 0.0)) scal[S_BREAK] = 1.0;
         }
     }
+}
+
+// ---------------------------------------------------------------------------------------------
+// BiCGStab building blocks (FP64), right preconditioning
+
+// y = A x with the non-symmetric operator; partials w1.y (and y.y when two_dots)
+__global__ void __launch_bounds__(LIN_BLOCK) k_matvec_ns(const OpNS A, const double* __restrict__ x,
+                                                         double* __restrict__ y,
+                                                         const double* __restrict__ w1,
+                                                         int two_dots,
+                                                         double* __restrict__ partials) {
+    double d1 = 0.0, d2 = 0.0;
+    const long long sz = (long long)A.nx * A.ny;
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < A.N;
+         c += (long long)gridDim.x * LIN_BLOCK) {
+        const int k = (int)(c / sz);
+        const long long rem = c - (long long)k * sz;
+        const int j = (int)(rem / A.nx), i = (int)(rem - (long long)j * A.nx);
+        const int q[3] = {i, j, k};
+        const int n[3] = {A.nx, A.ny, A.nz};
+        const long long s[3] = {1, A.nx, sz};
+        double off = 0.0;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const long long lo = q[ax] > 0 ? c - s[ax] : c + (long long)(n[ax] - 1) * s[ax];
+            off += A.Q[ax][c] * x[lo];                // 0 on zero-flux boundary faces
+            long long hi = -1;
+            if (q[ax] < n[ax] - 1) hi = c + s[ax];
+            else if (A.per[ax]) hi = c - (long long)(n[ax] - 1) * s[ax];
+            if (hi >= 0) off += A.P[ax][hi] * x[hi];
+        }
+        const double v = A.diag[c] * x[c] - A.scale * off;
+        y[c] = v;
+        d1 += w1[c] * v;
+        d2 += v * v;
+    }
+    const double s1 = block_sum<LIN_BLOCK>(d1);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s1;
+    if (two_dots) {
+        const double s2 = block_sum<LIN_BLOCK>(d2);
+        if (threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = s2;
+    }
+}
+
+// r = b, rh = b, x = 0; partial r.r
+__global__ void __launch_bounds__(LIN_BLOCK) k_bicg_init(long long N, const double* __restrict__ b,
+                                                         double* __restrict__ r,
+                                                         double* __restrict__ rh,
+                                                         double* __restrict__ x,
+                                                         double* __restrict__ partials) {
+    double acc = 0.0;
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+         c += (long long)gridDim.x * LIN_BLOCK) {
+        const double v = b[c];
+        r[c] = v;
+        rh[c] = v;
+        x[c] = 0.0;
+        acc += v * v;
+    }
+    const double s = block_sum<LIN_BLOCK>(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// p = r + beta (p - omega v); first: p = r
+__global__ void __launch_bounds__(LIN_BLOCK) k_bicg_p(long long N, const double* __restrict__ scal,
+                                                      const double* __restrict__ r,
+                                                      const double* __restrict__ v,
+                                                      double* __restrict__ p, int first) {
+    const double beta = scal[S_BETA], omega = scal[S_OMEGA];
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+         c += (long long)gridDim.x * LIN_BLOCK)
+        p[c] = first ? r[c] : r[c] + beta * (p[c] - omega * v[c]);
+}
+
+// s = r - alpha v; partial s.s
+__global__ void __launch_bounds__(LIN_BLOCK) k_bicg_s(long long N, const double* __restrict__ scal,
+                                                      const double* __restrict__ r,
+                                                      const double* __restrict__ v,
+                                                      double* __restrict__ s,
+                                                      double* __restrict__ partials) {
+    const double alpha = scal[S_ALPHA];
+    double acc = 0.0;
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+         c += (long long)gridDim.x * LIN_BLOCK) {
+        const double sv = r[c] - alpha * v[c];
+        s[c] = sv;
+        acc += sv * sv;
+    }
+    const double t = block_sum<LIN_BLOCK>(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// x += alpha ph + omega sh; r = s - omega t; partials r.r then rh.r
+__global__ void __launch_bounds__(LIN_BLOCK) k_bicg_xr(long long N, const double* __restrict__ scal,
+                                                       double* __restrict__ x,
+                                                       const double* __restrict__ ph,
+                                                       const double* __restrict__ sh,
+                                                       const double* __restrict__ s,
+                                                       const double* __restrict__ t,
+                                                       double* __restrict__ r,
+                                                       const double* __restrict__ rh,
+                                                       double* __restrict__ partials) {
+    const double alpha = scal[S_ALPHA], omega = scal[S_OMEGA];
+    double rr = 0.0, rhr = 0.0;
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+         c += (long long)gridDim.x * LIN_BLOCK) {
+        x[c] += alpha * ph[c] + omega * sh[c];
+        const double rv = s[c] - omega * t[c];
+        r[c] = rv;
+        rr += rv * rv;
+        rhr += rh[c] * rv;
+    }
+    const double a1 = block_sum<LIN_BLOCK>(rr);
+    if (threadIdx.x == 0) partials[blockIdx.x] = a1;
+    const double a2 = block_sum<LIN_BLOCK>(rhr);
+    if (threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = a2;
+}
+
+// x += scal[slot] p
+__global__ void __launch_bounds__(LIN_BLOCK) k_axpy(long long N, const double* __restrict__ scal,
+                                                    int slot, const double* __restrict__ p,
+                                                    double* __restrict__ x) {
+    const double a = scal[slot];
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+         c += (long long)gridDim.x * LIN_BLOCK)
+        x[c] += a * p[c];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -416,6 +560,47 @@ cudaError_t LinLaunch::cg_init(long long N, const double* b, double* r, double* 
 cudaError_t LinLaunch::reduce(const double* part, int n, double* scal, int op, int slot) {
     begin("reduce");
     k_reduce<<<1, RED_BLOCK, 0, st>>>(part, n, scal, op, slot);
+    return end();
+}
+
+cudaError_t LinLaunch::matvec_ns(const OpNS& A, const double* x, double* y, const double* w1,
+                                 int two_dots, double* part, int& nparts) {
+    nparts = stream_blocks(A.N);
+    begin("bicg_matvec");
+    k_matvec_ns<<<nparts, LIN_BLOCK, 0, st>>>(A, x, y, w1, two_dots, part);
+    return end();
+}
+cudaError_t LinLaunch::bicg_init(long long N, const double* b, double* r, double* rh, double* x,
+                                 double* part, int& nparts) {
+    nparts = stream_blocks(N);
+    begin("bicg_init");
+    k_bicg_init<<<nparts, LIN_BLOCK, 0, st>>>(N, b, r, rh, x, part);
+    return end();
+}
+cudaError_t LinLaunch::bicg_p(long long N, const double* scal, const double* r, const double* v,
+                              double* p, int first) {
+    begin("bicg_update_p");
+    k_bicg_p<<<stream_blocks(N), LIN_BLOCK, 0, st>>>(N, scal, r, v, p, first);
+    return end();
+}
+cudaError_t LinLaunch::bicg_s(long long N, const double* scal, const double* r, const double* v,
+                              double* s, double* part, int& nparts) {
+    nparts = stream_blocks(N);
+    begin("bicg_update_s");
+    k_bicg_s<<<nparts, LIN_BLOCK, 0, st>>>(N, scal, r, v, s, part);
+    return end();
+}
+cudaError_t LinLaunch::bicg_xr(long long N, const double* scal, double* x, const double* ph,
+                               const double* sh, const double* s, const double* t, double* r,
+                               const double* rh, double* part, int& nparts) {
+    nparts = stream_blocks(N);
+    begin("bicg_update_xr");
+    k_bicg_xr<<<nparts, LIN_BLOCK, 0, st>>>(N, scal, x, ph, sh, s, t, r, rh, part);
+    return end();
+}
+cudaError_t LinLaunch::axpy(long long N, const double* scal, int slot, const double* p, double* x) {
+    begin("axpy");
+    k_axpy<<<stream_blocks(N), LIN_BLOCK, 0, st>>>(N, scal, slot, p, x);
     return end();
 }
 

@@ -16,9 +16,23 @@ struct Op {
     T scale;
 };
 
-// device scalar slots of the CG iteration
-enum { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RR, S_BREAK, S_TMP, S_NSCAL = 8 };
-enum { RED_SUM = 0, RED_ALPHA = 1, RED_BETA = 2 };
+// Non-symmetric 7-point operator (the Schur matrix with dD/dE kept):
+// (A x)_c = diag_c x_c - scale * sum_ax (Q[ax]_c x_lo + P[ax]_hi x_hi), P and Q per lower face.
+struct OpNS {
+    int nx, ny, nz;
+    long long N;
+    int per[3];
+    const double* diag;
+    const double* P[3];
+    const double* Q[3];
+    double scale;
+};
+
+// device scalar slots of the Krylov iterations
+enum { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RR, S_BREAK, S_TMP, S_RHO, S_OMEGA, S_SS, S_TS,
+       S_TT, S_RV, S_NSCAL = 16 };
+enum { RED_SUM = 0, RED_ALPHA = 1, RED_BETA = 2, RED_BICG_ALPHA = 3, RED_BICG_OMEGA = 4,
+       RED_BICG_RHO = 5 };
 
 // number of blocks of the grid-stride streaming kernels (= number of partial sums)
 int stream_blocks(long long N);
@@ -48,6 +62,19 @@ struct LinLaunch {
     cudaError_t cg_init(long long N, const double* b, double* r, double* x, double* part,
                         int& nparts);
     cudaError_t reduce(const double* part, int n, double* scal, int op, int slot);
+    // BiCGStab (right-preconditioned) building blocks
+    cudaError_t matvec_ns(const OpNS& A, const double* x, double* y, const double* w1,
+                          int two_dots, double* part, int& nparts);
+    cudaError_t bicg_init(long long N, const double* b, double* r, double* rh, double* x,
+                          double* part, int& nparts);
+    cudaError_t bicg_p(long long N, const double* scal, const double* r, const double* v,
+                       double* p, int first);
+    cudaError_t bicg_s(long long N, const double* scal, const double* r, const double* v,
+                       double* s, double* part, int& nparts);
+    cudaError_t bicg_xr(long long N, const double* scal, double* x, const double* ph,
+                        const double* sh, const double* s, const double* t, double* r,
+                        const double* rh, double* part, int& nparts);
+    cudaError_t axpy(long long N, const double* scal, int slot, const double* p, double* x);
 
     template <typename T>
     cudaError_t smooth(const Op<T>& A, const T* b, const T* xin, T* xout, T omega, int first);

@@ -38,24 +38,56 @@ cudaError_t launch_kappa(const StepParams& P, int ns, const double* n, double* k
 //
 // R = |E_b - E_a| / (a dx Ebar) floored at R_min; with q = max(|dE|, R_min a dx Ebar) and
 // s = a dx Ebar, D = c s (2 kappa s + q) / (6 kappa^2 s^2 + 3 kappa q s + q^2): one division.
+//
+// With dD/dE kept in the Newton matrix (Sec. 3.2.1 lags only the opacity), the face between
+// lower cell a and upper cell b (dE = E_b - E_a) contributes dt theta P to b's diagonal and
+// -dt theta Q to (b, a), dt theta Q to a's diagonal and -dt theta P to (a, b), where
+// P = W + (dW/dE_b) dE and Q = W - (dW/dE_a) dE.  With R dD/dR = -c q^2 (4 kappa s + q) s / den^2
+// and t = dE / (E_a + E_b): P = W + R dD/dR (1 - t) / (a dx)^2, Q = W + R dD/dR (1 + t) / (a dx)^2
+// (both = W where R sits at its floor).
 
-__device__ __forceinline__ double face_coef(const StepParams& P, double Ea, double Eb,
-                                            double ka, double kb) {
+struct FaceCoef { double W, P, Q; };
+
+template <bool PQ>
+__device__ __forceinline__ FaceCoef face_coef(const StepParams& P, double Ea, double Eb,
+                                              double ka, double kb) {
     const double kap = 0.5 * (ka + kb);
+    FaceCoef r;
     if (P.limiter) {
-        const double s = 0.5 * (Ea + Eb) / P.inv_adx;          // a dx Ebar
-        const double q = fmax(fabs(Eb - Ea), P.R_min * s);
+        const double Esum = Ea + Eb;
+        const double s = 0.5 * Esum / P.inv_adx;               // a dx Ebar
+        const double dE = Eb - Ea;
+        const double qraw = fabs(dE);
+        const double q = fmax(qraw, P.R_min * s);
         const double ks = kap * s;
         const double num = C_LIGHT * s * (2.0 * ks + q);
         const double den = 6.0 * ks * ks + 3.0 * ks * q + q * q;
-        return num / den * P.inv_a2dx2;
+        if (!PQ) {
+            r.W = num / den * P.inv_a2dx2;
+            r.P = r.Q = r.W;
+            return r;
+        }
+        const double iden = 1.0 / den;
+        r.W = num * iden * P.inv_a2dx2;
+        if (qraw > P.R_min * s) {
+            const double RdD = -C_LIGHT * q * q * (4.0 * ks + q) * s * iden * iden * P.inv_a2dx2;
+            const double t = dE / Esum;
+            r.P = r.W + RdD * (1.0 - t);
+            r.Q = r.W + RdD * (1.0 + t);
+        } else {
+            r.P = r.Q = r.W;
+        }
+        return r;
     }
-    return C_LIGHT / (3.0 * fmax(kap, P.kappa_floor)) * P.inv_a2dx2;
+    r.W = C_LIGHT / (3.0 * fmax(kap, P.kappa_floor)) * P.inv_a2dx2;
+    r.P = r.Q = r.W;
+    return r;
 }
 
+template <bool PQ>
 __global__ void __launch_bounds__(256) k_faces(const StepParams P, const double* __restrict__ E,
                                                const double* __restrict__ kap,
-                                               double* __restrict__ W) {
+                                               double* __restrict__ W, double* __restrict__ PQv) {
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= P.N) return;
     int i, j, k;
@@ -64,16 +96,49 @@ __global__ void __launch_bounds__(256) k_faces(const StepParams P, const double*
     const double Ec = E[c], kc = kap[c];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-        double w = 0.0;
-        if (b.has_lo[ax]) w = face_coef(P, E[b.lo[ax]], Ec, kap[b.lo[ax]], kc);
-        W[ax * P.N + c] = w;
+        FaceCoef f{0.0, 0.0, 0.0};
+        if (b.has_lo[ax]) f = face_coef<PQ>(P, E[b.lo[ax]], Ec, kap[b.lo[ax]], kc);
+        W[ax * P.N + c] = f.W;
+        if (PQ) {
+            PQv[ax * P.N + c] = f.P;
+            PQv[(3 + ax) * P.N + c] = f.Q;
+        }
     }
 }
 
 cudaError_t launch_faces(const StepParams& P, const double* E, const double* kap, double* W,
-                         cudaStream_t st) {
+                         double* PQ, cudaStream_t st) {
     const int b = 256;
-    k_faces<<<(unsigned)((P.N + b - 1) / b), b, 0, st>>>(P, E, kap, W);
+    const unsigned g = (unsigned)((P.N + b - 1) / b);
+    if (PQ) k_faces<true><<<g, b, 0, st>>>(P, E, kap, W, PQ);
+    else k_faces<false><<<g, b, 0, st>>>(P, E, kap, W, nullptr);
+    return cudaGetLastError();
+}
+
+// Newton-matrix face entries of each cell for inspection: S_lo[ax] couples a cell to its
+// lower neighbour, S_hi[ax] to its upper neighbour (positive numbers; the matrix entries are
+// their negatives; 0 where the face carries no flux).
+__global__ void k_export_faces(const StepParams P, const double* __restrict__ W,
+                               const double* __restrict__ PQ, double* __restrict__ lo,
+                               double* __restrict__ hi) {
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= P.N) return;
+    int i, j, k;
+    cell_coords(P, c, i, j, k);
+    const Nbr b = neighbours(P, c, i, j, k);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const double* Qa = PQ ? PQ + (3 + ax) * P.N : W + ax * P.N;
+        const double* Pa = PQ ? PQ + ax * P.N : W + ax * P.N;
+        lo[ax * P.N + c] = P.dth * Qa[c];
+        hi[ax * P.N + c] = b.has_hi[ax] ? P.dth * Pa[b.hi[ax]] : 0.0;
+    }
+}
+
+cudaError_t launch_export_faces(const StepParams& P, const double* W, const double* PQ,
+                                double* S_lo, double* S_hi, cudaStream_t st) {
+    const int b = 256;
+    k_export_faces<<<(unsigned)((P.N + b - 1) / b), b, 0, st>>>(P, W, PQ, S_lo, S_hi);
     return cudaGetLastError();
 }
 
@@ -285,14 +350,19 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const P
         const double eh = B.eh[c], nH = B.nH[c], src = B.src[c];
         const double Tfix = P.isothermal ? B.Tiso[c] : 0.0;
 
-        // diffusion: sum over faces W (E_c - E_nb), with W frozen (lagged D)
-        double Dterm = 0.0, Wsum = 0.0;
+        // diffusion: sum over faces W (E_c - E_nb); W sum for the lagged-D diagonal and, with
+        // dD/dE kept, the Newton-matrix diagonal sum (P of own lower faces, Q of upper faces)
+        double Dterm = 0.0, Wsum = 0.0, PQsum = 0.0;
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
             const double wlo = B.W[ax * N + c];
             const double whi = nb.has_hi[ax] ? B.W[ax * N + nb.hi[ax]] : 0.0;
             Dterm += wlo * (E - En[nb.lo[ax]]) + whi * (E - En[nb.hi[ax]]);
             Wsum += wlo + whi;
+            if (MODE != MODE_PREP_PREDICT && B.PQ) {
+                PQsum += B.PQ[ax * N + c];
+                if (nb.has_hi[ax]) PQsum += B.PQ[(3 + ax) * N + nb.hi[ax]];
+            }
         }
 
         Local<NS> lo;
@@ -325,7 +395,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const P
             for (int v = 0; v < NV; ++v) d[v] = -P.dt * Lf[v];
             double cap = 1.0;
             auto bound = [&](double q, double dq, double tiny) {
-                if (dq < -tiny) cap = fmin(cap, fmax(P.tau * q / (-dq), 0.0));
+                if (dq < 0.0) cap = fmin(cap, fmax(P.tau * (q + tiny) / (-dq), 0.0));
             };
             bound(eh + ec, d[0], 0.0);
             bound(E, d[NV - 1], 0.0);
@@ -373,6 +443,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const P
 #pragma unroll
             for (int r = 0; r < NM; ++r) { LMU += Lr[r] * z[r]; LMf += Lr[r] * y[r]; }
             B.diag[c] = Dloc - LMU + P.dth * Wsum;
+            if (B.PQ) B.diag_ns[c] = Dloc - LMU + P.dth * PQsum;
             B.rhs[c] = LMf - fs[NV - 1];
 #pragma unroll
             for (int r = 0; r < NM; ++r) {
@@ -403,7 +474,9 @@ cudaError_t launch_cell(const StepParams& P, int ns, int mode, const PhysBuffers
 }
 
 // ---------------------------------------------------------------------------------------------
-// Newton update: step (iii) recovery, positivity cap, line-search fraction, new opacity
+// Newton update: step (iii) recovery, positivity cap, line-search fraction, new opacity.
+// The cap keeps every bounded quantity q (e, E: bound 0; species: bound -1e-13 of the element
+// total) above its bound by (1 - tau) of its current distance q + tiny.
 
 template <int NS>
 __global__ void __launch_bounds__(256) k_update(const StepParams P, double lam,
@@ -434,7 +507,7 @@ __global__ void __launch_bounds__(256) k_update(const StepParams P, double lam,
     const double E = E0[c], nH = nHa[c];
     double cap = 1.0;
     auto bound = [&](double q, double dq, double tiny) {
-        if (dq < -tiny) cap = fmin(cap, fmax(P.tau * q / (-dq), 0.0));
+        if (dq < 0.0) cap = fmin(cap, fmax(P.tau * (q + tiny) / (-dq), 0.0));
     };
     bound(eh[c] + ec, s[0], 0.0);
     bound(E, sEp, 0.0);

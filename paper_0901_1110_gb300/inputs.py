@@ -150,7 +150,18 @@ def config_uniform_32():
     return uniform_h(32, name="uniform_h_32")
 
 
-def config_lognormal(n=128, nsrc=16, seed=0):
+# Radiation scaling u_E of the source-driven lognormal runs: a round number of the order of the
+# energy density a median source (1e49 photons/s of mean energy ~47 eV) keeps one 3.9 kpc cell
+# away, L <h nu> / (c dx^2) ~ 1.1e-16 erg/cm^3, so that scaled E is O(1-10) where the sources
+# act (the 1e-20 ambient floor would put it at 1e5 there).
+U_E_SOURCES = 1e-16
+
+
+def config_lognormal(n=128, nsrc=16, seed=0, box=1.0 * MPC):
     """H + He lognormal medium (sigma_ln = 1, P(k) ~ k^-2, mean n_H = 1e-3), lognormal point
-    sources (median 1e49 s^-1), 20 steps of 5e12 s; 128^3 with 16 sources or 256^3 with 64."""
-    return lognormal_hhe((n, n, n), seed=seed, nsrc=nsrc, name=f"lognormal_hhe_{n}")
+    sources (median 1e49 s^-1), 20 steps of 5e12 s, theta = 1; 128^3 with 16 sources or 256^3
+    with 64 in a 1 Mpc box (sub-boxes keep the 256^3 cell size with box = n / 256 Mpc)."""
+    w = lognormal_hhe((n, n, n), box=box, seed=seed, nsrc=nsrc, name=f"lognormal_hhe_{n}")
+    w.theta = 1.0
+    w.u_E = U_E_SOURCES
+    return w

@@ -66,14 +66,16 @@ def test_grey_constants_match_oracle_quadrature(rhi):
         assert abs(a["eps"] / b["eps"] - 1) < 1e-12
 
 
+@pytest.mark.parametrize("ljac", [0, 1])
 @pytest.mark.parametrize("name", list(WL))
-def test_linear_system_matches_oracle(rhi, name):
+def test_linear_system_matches_oracle(rhi, name, ljac):
     """Residual f(U^n) (eq. nonlinear_residual), Schur matrix S = D - L M^-1 U and right-hand
-    side L M^-1 f_M - f_E (Sec. 3.2.1) of the first Newton system, cell by cell."""
+    side L M^-1 f_M - f_E (Sec. 3.2.1) of the first Newton system, cell by cell, with D lagged
+    (symmetric S) and with dD/dE kept (non-symmetric S)."""
     w = WL[name]
-    s = rhi.solver_for_workload(w)
+    s = rhi.solver_for_workload(w, limiter_jacobian=ljac)
     lin = s.linearize(w.dt)
-    p = oracle_problem(w)
+    p = oracle_problem(w, limiter_jacobian="E" if ljac else "lagged")
     st = w.state()
     U = md.state_to_U(p, st)
     g = md.build_g(p, U, st["e"], w.dt, 1.0, 0.0)
@@ -86,15 +88,17 @@ def test_linear_system_matches_oracle(rhi, name):
     # the Schur diagonal and right-hand side subtract L M^-1 U / L M^-1 f_M: cancellation
     np.testing.assert_allclose(lin["diag"], S.diagonal(), rtol=TOL_FP64)
     np.testing.assert_allclose(lin["rhs"], rhs, rtol=TOL_FP64, atol=1e-12 * np.abs(rhs).max())
-    # off-diagonals: face between a cell and its lower neighbour along x, y, z
+    # face entries: a cell's coupling to its lower (d = 2 ax) and upper (2 ax + 1) neighbours
     nb, valid = md.neighbor_table(p)
     Sd = S.tocsr()
+    dims = (p.nx, p.ny, p.nz)
     for ax in range(3):
-        d = 2 * ax
-        want = np.where(valid[d], -np.asarray(Sd[np.arange(p.N), nb[d]]).ravel(), 0.0)
-        if p.bc[d] == "periodic" and (p.nx, p.ny, p.nz)[ax] <= 2:
-            continue
-        np.testing.assert_allclose(lin["face"][ax], want, rtol=1e-12, atol=1e-300)
+        if p.bc[2 * ax] == "periodic" and dims[ax] <= 2:
+            continue                      # both faces join the same pair of cells
+        for d, key in ((2 * ax, "face"), (2 * ax + 1, "face_hi")):
+            want = np.where(valid[d], -np.asarray(Sd[np.arange(p.N), nb[d]]).ravel(), 0.0)
+            scale = max(np.abs(want).max(), 1e-300)
+            assert np.abs(lin[key][ax] - want).max() <= 1e-11 * scale, (ax, key)
 
 
 @pytest.mark.parametrize("name", list(WL))
@@ -112,6 +116,22 @@ def test_steps_match_oracle(rhi, name, precond):
         s.step(w.dt, 1.0, 0.0, newton_tol=1e-12, lin_tol=1e-12)
         ref, stats = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, 1e-13, linear="direct")
         assert stats["converged"]
+        err = _field_errors(s.get_state(), ref)
+        assert max(err.values()) <= TOL_FP64, (step, err, s.stats())
+
+
+@pytest.mark.parametrize("name", ["lognormal_hhe", "lognormal_hhe_periodic", "uniform_h_ragged"])
+def test_steps_with_dD_dE_match_oracle(rhi, name):
+    """The Newton matrix that keeps dD/dE (BiCGStab on the non-symmetric Schur matrix,
+    preconditioned by the FP32 V-cycle) reaches the same solution as the oracle."""
+    w = WL[name]
+    s = rhi.solver_for_workload(w, precond=rhi.RHI_PRECOND_MG_FP32, mg_levels=4,
+                                limiter_jacobian=1)
+    p = oracle_problem(w)
+    ref = w.state()
+    for step in range(w.nsteps):
+        s.step(w.dt, 1.0, 0.0, newton_tol=1e-12, lin_tol=1e-12)
+        ref, stats = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, 1e-13, linear="direct")
         err = _field_errors(s.get_state(), ref)
         assert max(err.values()) <= TOL_FP64, (step, err, s.stats())
 

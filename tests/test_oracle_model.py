@@ -35,7 +35,7 @@ def _random_state(p, rng, T_range=(50.0, 1e6), E_scale=1e-17):
     return U, eh
 
 
-def _fd_jacobian(p, U, g, eh, dt, a, adot, T_fixed, W):
+def _fd_jacobian(p, U, g, eh, dt, a, adot, T_fixed, W=None, kap_faces=None):
     u = p.scales()
     Jfd = np.zeros((p.nv * p.N, p.nv * p.N))
     for v in range(p.nv):
@@ -43,8 +43,8 @@ def _fd_jacobian(p, U, g, eh, dt, a, adot, T_fixed, W):
             h = 1e-6 * max(abs(U[v, c]), 1e-3 * u[v])
             Up = U.copy(); Up[v, c] += h
             Um = U.copy(); Um[v, c] -= h
-            fp = md.residual(p, Up, g, eh, dt, a, adot, T_fixed, W=W) / u[:, None]
-            fm = md.residual(p, Um, g, eh, dt, a, adot, T_fixed, W=W) / u[:, None]
+            fp = md.residual(p, Up, g, eh, dt, a, adot, T_fixed, W=W, kap_faces=kap_faces) / u[:, None]
+            fm = md.residual(p, Um, g, eh, dt, a, adot, T_fixed, W=W, kap_faces=kap_faces) / u[:, None]
             Jfd[:, v * p.N + c] = ((fp - fm) / (2 * h) * u[v]).ravel()
     return Jfd
 
@@ -72,6 +72,38 @@ def test_jacobian_matches_central_differences(ns, isothermal, a, adot):
     Jfd = _fd_jacobian(p, U, g, eh, w.dt, a, adot, T_fixed, W)
     scale = np.abs(Jfd).max(axis=1, keepdims=True)
     assert np.max(np.abs(J - Jfd) / scale) < 1e-6
+
+
+@pytest.mark.parametrize("ns", [1, 3])
+def test_jacobian_with_dD_dE_matches_central_differences(ns):
+    """Sec. 3.2.1: the Newton matrix that keeps the limiter's E dependence and lags only its
+    opacity equals central differences of f with the face opacities frozen, including faces
+    in the free-streaming regime (steep E contrasts, thin cells)."""
+    rng = np.random.default_rng(40 + ns)
+    if ns == 1:
+        w = inputs.uniform_h(3, shape=(2, 3, 4), box=60 * KPC, dt=3e13, bc=("periodic",) * 6)
+    else:
+        w = inputs.lognormal_hhe((2, 3, 4), box=60 * KPC, nsrc=2, dt=3e13)
+    p = oracle_problem(w, rates=cl.SmoothRates(), theta=0.8, limiter_jacobian="E")
+    U, eh = _random_state(p, rng)
+    U[1 + ns] = 1e-17 * np.exp(rng.uniform(-6.0, 6.0, p.N))     # strong gradients
+    U[1] = p.nH * rng.uniform(1e-6, 1e-4, p.N)                   # ionised: optically thin
+    if ns == 3:
+        U[2] = p.y_he * p.nH * rng.uniform(1e-6, 1e-4, p.N)
+    Un = md.state_to_U(p, w.state())
+    g = md.build_g(p, Un, w.e.ravel(), w.dt, 1.0, 0.0)
+    lt = md.local_terms(p, U[0], U[1:1 + ns], U[1 + ns], eh, p.nH, p.src, 1.0, 0.0)
+    J = md.full_jacobian(p, U, eh, w.dt, 1.0, 0.0).toarray()
+    Jfd = _fd_jacobian(p, U, g, eh, w.dt, 1.0, 0.0, None, kap_faces=lt["kappa"])
+    scale = np.abs(Jfd).max(axis=1, keepdims=True)
+    # the limiter is strongly nonlinear across these contrasts: central differences with a
+    # 1e-6 step carry ~1e-6..1e-5 truncation error here; a wrong term shows up at O(1)
+    assert np.max(np.abs(J - Jfd) / scale) < 3e-5
+    # and it is not symmetric (the E block carries the limiter's advective part)
+    nm = ns + 1
+    JE = J[nm * p.N:, nm * p.N:]
+    off = JE - np.diag(np.diag(JE))
+    assert np.abs(off - off.T).max() > 1e-2 * np.abs(off).max()
 
 
 def test_limiter_limits():
@@ -224,8 +256,9 @@ def test_photon_number_conservation_periodic_box(theta):
     assert abs(photons(new) - photons(st)) > 1e-3 * photons(st)   # photons were absorbed
 
 
+@pytest.mark.parametrize("ljac", ["lagged", "E"])
 @pytest.mark.parametrize("ns,bc", [(1, "zero_flux"), (3, "zero_flux"), (3, "periodic")])
-def test_schur_reduction_equals_unreduced_solve(ns, bc):
+def test_schur_reduction_equals_unreduced_solve(ns, bc, ljac):
     """Sec. 3.2.1 steps (i)-(iii) (eqs. newton_system2, schur_components, step_ia) give the
     same Newton correction as a direct solve of the whole unreduced system."""
     rng = np.random.default_rng(ns)
@@ -234,7 +267,7 @@ def test_schur_reduction_equals_unreduced_solve(ns, bc):
     else:
         w = inputs.lognormal_hhe((3, 4, 5), box=80 * KPC, nsrc=2, dt=3e13, bc=(bc,) * 6)
     w.theta = 0.8
-    p = oracle_problem(w)
+    p = oracle_problem(w, limiter_jacobian=ljac)
     U, eh = _random_state(p, rng, T_range=(100, 1e5))
     Un = md.state_to_U(p, w.state())
     g = md.build_g(p, Un, w.e.ravel(), w.dt, 1.0, 0.0)
@@ -293,6 +326,24 @@ def test_newton_linear_solvers_agree_and_conserve_elements():
     nHI, nHeI, nHeII = ref["n"]
     assert np.all(nHI > 0) and np.all(nHI < p.nH)
     assert np.all(nHeI > 0) and np.all(nHeII > 0) and np.all(nHeI + nHeII < nHe)
+
+
+def test_newton_with_dD_dE_reaches_the_same_root():
+    """Keeping dD/dE (Sec. 3.2.1) changes only the path: both Newton matrices reach the same
+    root of f(U) = 0 where the radiation free-streams (small box, ionised bubbles)."""
+    w = inputs.lognormal_hhe((10, 11, 12), box=50 * KPC, nsrc=3, dt=5e12)
+    w.theta = 1.0
+    st = w.state()
+    p0 = oracle_problem(w, u_E=1e-17)
+    st1, _ = sv.implicit_step(p0, st, w.dt, 1.0, 0.0, 1e-10, linear="direct")   # bubbles form
+    out = {}
+    for lj in ("lagged", "E"):
+        p = oracle_problem(w, u_E=1e-17, limiter_jacobian=lj)
+        out[lj], stats = sv.implicit_step(p, st1, w.dt, 1.0, 0.0, 1e-11, linear="direct")
+        assert stats["converged"], (lj, stats["res_history"])
+    for key in ("E", "e", "n"):
+        d = np.abs(out["E"][key] - out["lagged"][key]).max() / np.abs(out["lagged"][key]).max()
+        assert d < 1e-9, (key, d)
 
 
 def test_rms_norm_definition():
