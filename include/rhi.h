@@ -71,6 +71,7 @@ typedef struct {
     double u_e, u_n, u_E;   /* scalings of eq. scalings: erg/g, cm^-3, erg/cm^3               */
     double tau;             /* fraction-to-boundary of the positivity cap (0 < tau < 1)      */
     double lam_min;         /* smallest line-search parameter                                */
+    double mlp_gate;        /* learned guess: predicted changes below this keep U^n          */
     double growth_max;      /* watchdog line search: a full step may raise ||f|| up to
                                growth_max times the best ||f|| of the step ...               */
     int watchdog;           /* ... for at most this many Newton iterations in a row          */
@@ -180,6 +181,41 @@ int rhi_precond_apply(rhi_handle h, const double* r, double* z, int on_device);
    launch count) and returns the number of kernels (>= 0) or -RHI_ERR_*. */
 int rhi_set_profiling(rhi_handle h, int on);
 int rhi_kernel_times(rhi_handle h, int max, char* names, double* total_ms, int* launches);
+
+/* Learned Newton initial guess (an addition; Sec. 3.2 leaves the initial iterate free): a
+   per-cell MLP 9 -> 64 -> 64 -> 64 -> 6 with SiLU predicting the state at t^{n+1} from the
+   state at t^n.  Features: log10 E/u_E, log10 e/u_e, log10 of the HI, HeI, HeII fractions,
+   log10 n_H/u_n, log10(dt Gamma_HI + 1e-30), log10(1 + 4 pi eta dt / E), log10(dt / 1e12 s).
+   Outputs: log10 E'/E, log10 e'/e, logit of x_HI', logits of the He fractions (softmax).
+   Weights (FP32, RHI_MLP_NWEIGHTS): W1 (64x9, row major), b1 (64), W2 (64x64), b2, W3
+   (64x64), b3, W4 (6x64), b4 (6), then the input normalisation mean (9) and scale (9).
+   Inference uses BF16 copies on the tensor cores with FP32 accumulation; training updates
+   the FP32 weights with Adam using FP32 forward / backward kernels.  With guess =
+   RHI_GUESS_LEARNED a step evaluates ||f|| at U^n and at the network's guess (cells whose
+   predicted changes are all below params.mlp_gate keep U^n) and starts Newton from the
+   smaller; rhi_stats.guess_used says which. */
+#define RHI_MLP_IN 9
+#define RHI_MLP_HID 64
+#define RHI_MLP_OUT 6
+#define RHI_MLP_NWEIGHTS (64 * 9 + 64 + 64 * 64 + 64 + 64 * 64 + 64 + 6 * 64 + 6 + 9 + 9)
+int rhi_mlp_set_weights(rhi_handle h, const float* w, size_t n);
+int rhi_mlp_get_weights(rhi_handle h, float* w, size_t n);
+/* Features (N x 9, FP32) of the current state for a step of length dt at expansion a. */
+int rhi_mlp_features(rhi_handle h, double dt, double a, float* X, int on_device);
+/* Training targets (N x 6, FP32) of the step from the given earlier state (E, e, n as in
+   rhi_set_state) to the current state. */
+int rhi_mlp_targets(rhi_handle h, const double* E_old, const double* e_old,
+                    const double* n_old, float* Y, int on_device);
+/* Network outputs Y (n x 6) for features X (n x 9) on the tensor cores (BF16 weights). */
+int rhi_mlp_forward(rhi_handle h, const float* X, float* Y, long long n, int on_device);
+/* Mean squared error over the n samples and its gradient wrt the FP32 weights (FP32
+   forward / backward; the normalisation entries get 0). */
+int rhi_mlp_loss_grad(rhi_handle h, const float* X, const float* Y, long long n, float* grad,
+                      double* loss, int on_device);
+/* Adam (beta 0.9 / 0.999) over the n samples in minibatches of `batch`, `epochs` passes, in
+   sample order; writes the mean loss of the last epoch.  X and Y are device pointers. */
+int rhi_mlp_train(rhi_handle h, const float* X, const float* Y, long long n, int epochs,
+                  int batch, double lr, double* loss);
 
 /* Allocation-free RMS norm (no counterpart in the paper; an addition for callers that may
    not allocate device memory, such as code running while a stream is captured into a CUDA

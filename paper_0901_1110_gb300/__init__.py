@@ -33,7 +33,7 @@ class rhi_params(C.Structure):
                 ("m_grey", C.c_int), ("isothermal", C.c_int), ("limiter", C.c_int),
                 ("kappa_floor", C.c_double), ("u_e", C.c_double), ("u_n", C.c_double),
                 ("u_E", C.c_double), ("tau", C.c_double), ("lam_min", C.c_double),
-                ("growth_max", C.c_double), ("watchdog", C.c_int), ("limiter_jacobian", C.c_int),
+                ("mlp_gate", C.c_double), ("growth_max", C.c_double), ("watchdog", C.c_int), ("limiter_jacobian", C.c_int),
                 ("max_newton", C.c_int), ("max_pcg", C.c_int), ("guess", C.c_int),
                 ("precond", C.c_int), ("mg_levels", C.c_int), ("mg_pre", C.c_int),
                 ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double),
@@ -68,6 +68,13 @@ _SIGS = {
     "rhi_set_profiling": (C.c_int, [_P, C.c_int]),
     "rhi_kernel_times": (C.c_int, [_P, C.c_int, C.c_char_p, _D, C.POINTER(C.c_int)]),
     "rhi_rms_norm_noalloc": (C.c_int, [_P, C.c_longlong, C.c_longlong, _P, _P]),
+    "rhi_mlp_set_weights": (C.c_int, [_P, _P, C.c_size_t]),
+    "rhi_mlp_get_weights": (C.c_int, [_P, _P, C.c_size_t]),
+    "rhi_mlp_features": (C.c_int, [_P, C.c_double, C.c_double, _P, C.c_int]),
+    "rhi_mlp_targets": (C.c_int, [_P, _P, _P, _P, _P, C.c_int]),
+    "rhi_mlp_forward": (C.c_int, [_P, _P, _P, C.c_longlong, C.c_int]),
+    "rhi_mlp_loss_grad": (C.c_int, [_P, _P, _P, C.c_longlong, _P, _D, C.c_int]),
+    "rhi_mlp_train": (C.c_int, [_P, _P, _P, C.c_longlong, C.c_int, C.c_int, C.c_double, _D]),
     "rhi_last_error": (C.c_char_p, [_P]),
     "rhi_status_string": (C.c_char_p, [C.c_int]),
     "rhi_destroy": (None, [_P]),
@@ -118,6 +125,9 @@ def rhi_grey_constants(spectrum, param, n_species):
 
 
 RHI_NOALLOC_MAX_COUNT = 33554432
+RHI_MLP_IN, RHI_MLP_HID, RHI_MLP_OUT = 9, 64, 6
+RHI_MLP_NWEIGHTS = (RHI_MLP_HID * RHI_MLP_IN + RHI_MLP_HID + 2 * (RHI_MLP_HID * RHI_MLP_HID + RHI_MLP_HID)
+                    + RHI_MLP_OUT * RHI_MLP_HID + RHI_MLP_OUT + 2 * RHI_MLP_IN)
 
 
 def rhi_rms_norm_noalloc(v_ptr, n, count, out_ptr, stream=None):
@@ -128,6 +138,21 @@ def rhi_rms_norm_noalloc(v_ptr, n, count, out_ptr, stream=None):
 
 def rhi_status_string(code):
     return lib().rhi_status_string(code).decode()
+
+
+def _fptr(a, count=None):
+    """(pointer, on_device) of a float32 numpy array or tensor, C-contiguous."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("arrays must be C-contiguous float32")
+        ptr, dev = a.ctypes.data, 0
+    else:
+        if str(a.dtype) != "torch.float32" or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float32")
+        ptr, dev = a.data_ptr(), (1 if a.is_cuda else 0)
+    if count is not None and (a.size if isinstance(a, np.ndarray) else a.numel()) < count:
+        raise ValueError("buffer too small")
+    return ptr, dev
 
 
 def _ptr(a):
@@ -234,6 +259,73 @@ class Solver:
         self._check(lib().rhi_precond_apply(self.h, r.ctypes.data, z.ctypes.data, 0),
                     "rhi_precond_apply")
         return z
+
+    # ---- learned guess (an addition to the paper's method) --------------------------------------
+
+    def mlp_set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32).ravel()
+        return self._check(lib().rhi_mlp_set_weights(self.h, w.ctypes.data, w.size),
+                           "rhi_mlp_set_weights")
+
+    def mlp_get_weights(self):
+        w = np.empty(RHI_MLP_NWEIGHTS, dtype=np.float32)
+        self._check(lib().rhi_mlp_get_weights(self.h, w.ctypes.data, w.size), "rhi_mlp_get_weights")
+        return w
+
+    def mlp_features(self, dt, a=1.0, out=None):
+        """Features (N x 9, float32) of the current state; into `out` (array or tensor) if given."""
+        X = np.empty((self.N, RHI_MLP_IN), dtype=np.float32) if out is None else out
+        pX, dev = _fptr(X, self.N * RHI_MLP_IN)
+        self._check(lib().rhi_mlp_features(self.h, dt, a, pX, dev), "rhi_mlp_features")
+        return X
+
+    def mlp_targets(self, old, out=None):
+        """Targets (N x 6, float32) of the step from `old` (dict E, e, n) to the current state."""
+        Y = np.empty((self.N, RHI_MLP_OUT), dtype=np.float32) if out is None else out
+        pY, dev = _fptr(Y, self.N * RHI_MLP_OUT)
+        (pE, d0), (pe, d1), (pn, d2) = _ptr(old["E"]), _ptr(old["e"]), _ptr(old["n"])
+        if len({d0, d1, d2, dev}) != 1:
+            raise TypeError("all buffers on the host or all on the device")
+        self._check(lib().rhi_mlp_targets(self.h, pE, pe, pn, pY, dev), "rhi_mlp_targets")
+        return Y
+
+    def mlp_forward(self, X, out=None):
+        n = X.shape[0]
+        Y = np.empty((n, RHI_MLP_OUT), dtype=np.float32) if out is None else out
+        (pX, d0), (pY, d1) = _fptr(X, n * RHI_MLP_IN), _fptr(Y, n * RHI_MLP_OUT)
+        if d0 != d1:
+            raise TypeError("X and Y both on the host or both on the device")
+        self._check(lib().rhi_mlp_forward(self.h, pX, pY, n, d0), "rhi_mlp_forward")
+        return Y
+
+    def mlp_loss_grad(self, X, Y):
+        n = X.shape[0]
+        (pX, d0), (pY, d1) = _fptr(X, n * RHI_MLP_IN), _fptr(Y, n * RHI_MLP_OUT)
+        if d0 != d1:
+            raise TypeError("X and Y both on the host or both on the device")
+        g = np.empty(RHI_MLP_NWEIGHTS, dtype=np.float32)
+        loss = C.c_double()
+        if d0:
+            import torch
+            gd = torch.empty(RHI_MLP_NWEIGHTS, dtype=torch.float32, device=X.device)
+            self._check(lib().rhi_mlp_loss_grad(self.h, pX, pY, n, gd.data_ptr(), C.byref(loss), 1),
+                        "rhi_mlp_loss_grad")
+            g = gd.cpu().numpy()
+        else:
+            self._check(lib().rhi_mlp_loss_grad(self.h, pX, pY, n, g.ctypes.data, C.byref(loss), 0),
+                        "rhi_mlp_loss_grad")
+        return loss.value, g
+
+    def mlp_train(self, X, Y, epochs=1, batch=4096, lr=1e-3):
+        """Adam over device tensors X (n x 9), Y (n x 6); returns the last epoch's mean loss."""
+        n = X.shape[0]
+        (pX, d0), (pY, d1) = _fptr(X, n * RHI_MLP_IN), _fptr(Y, n * RHI_MLP_OUT)
+        if not (d0 and d1):
+            raise TypeError("training data must be on the device")
+        loss = C.c_double()
+        self._check(lib().rhi_mlp_train(self.h, pX, pY, n, epochs, batch, lr, C.byref(loss)),
+                    "rhi_mlp_train")
+        return loss.value
 
     def set_profiling(self, on):
         return self._check(lib().rhi_set_profiling(self.h, int(on)), "rhi_set_profiling")

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librhi.so")
 
 SOURCES = ["rhi_host.cu", "rhi_closure.cu", "rhi_physics.cu", "rhi_linear.cu",
-           "rhi_noalloc.cu"]
+           "rhi_noalloc.cu", "rhi_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "rhi_linear.cuh"
+#include "rhi_mlp.cuh"
 
 using namespace rhi;
 
@@ -126,6 +127,16 @@ struct rhi_ctx {
     OpNS opns{};
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    // learned guess: FP32 master weights, Adam moments, gradient, BF16 inference copy;
+    // scratch of the training / inspection entry points grows on demand
+    float *mlp_w = nullptr, *mlp_m1 = nullptr, *mlp_m2 = nullptr, *mlp_g = nullptr;
+    MlpPacked* mlp_pk = nullptr;
+    bool mlp_ready = false;
+    long long mlp_t = 0;                  // Adam steps taken
+    struct Scratch { void* p = nullptr; size_t bytes = 0; };
+    Scratch mlp_scr[6];                   // act, del, partials, X, Y, grad staging
+    ~rhi_ctx() { for (auto& s : mlp_scr) if (s.p) cudaFree(s.p); }
 };
 
 namespace {
@@ -504,12 +515,79 @@ int validate_params(const rhi_params* p) {
     if (!(p->lam_min > 0.0 && p->lam_min <= 1.0)) return 0;
     if (!(p->growth_max >= 1.0) || p->watchdog < 0) return 0;
     if (p->max_newton < 0 || p->max_pcg < 1) return 0;
-    if (p->guess < 0 || p->guess > RHI_GUESS_PREDICTOR) return 0;
+    if (p->guess < 0 || p->guess > RHI_GUESS_LEARNED) return 0;
+    if (!(p->mlp_gate >= 0.0)) return 0;
     if (p->precond < 0 || p->precond > RHI_PRECOND_MG_FP32) return 0;
     if (p->mg_levels < 1 || p->mg_pre < 1 || p->mg_post < 0 || p->mg_coarse_sweeps < 1) return 0;
     if (p->limiter_jacobian != 0 && p->limiter_jacobian != 1) return 0;
     if (!(p->mg_omega > 0.0 && p->mg_omega <= 1.0)) return 0;
     return 1;
+}
+
+// ---- learned guess helpers
+
+enum { SCR_ACT = 0, SCR_DEL, SCR_PART, SCR_X, SCR_Y, SCR_G };
+
+template <typename T>
+int scratch(rhi_ctx* h, int slot, size_t count, T** out) {
+    rhi_ctx::Scratch& s = h->mlp_scr[slot];
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    if (s.bytes < bytes) {
+        if (s.p) CK(cudaStreamSynchronize(h->st));
+        if (s.p) cudaFree(s.p);
+        s.p = nullptr;
+        s.bytes = 0;
+        CK(cudaMalloc(&s.p, bytes));
+        s.bytes = bytes;
+    }
+    *out = (T*)s.p;
+    return RHI_OK;
+}
+
+MlpArgs mlp_args(const rhi_ctx* h, double dt, double a) {
+    MlpArgs A{};
+    A.N = h->N;
+    A.ns = h->ns;
+    A.y_he = h->prm.y_he;
+    A.iu_E = 1.0 / h->prm.u_E;
+    A.iu_e = 1.0 / h->prm.u_e;
+    A.iu_n = 1.0 / h->prm.u_n;
+    A.dt = dt;
+    A.gam_per_E = C_LIGHT * h->prm.pgam[0] / (a * a * a);
+    A.E = h->E_s; A.e = h->e_s; A.n = h->n_s; A.nH = h->nH; A.src = h->src;
+    A.gate = (float)h->prm.mlp_gate;
+    A.isothermal = h->prm.isothermal;
+    return A;
+}
+
+// host copy of the master weights -> BF16 inference copy on the device
+int mlp_repack(rhi_ctx* h) {
+    std::vector<float> w(RHI_MLP_NWEIGHTS);
+    CK(cudaMemcpyAsync(w.data(), h->mlp_w, w.size() * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    MlpPacked pk;
+    mlp_pack(w.data(), &pk);
+    CK(cudaMemcpyAsync(h->mlp_pk, &pk, sizeof pk, cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return RHI_OK;
+}
+
+// forward + backward of m samples (device X, Y) into h->mlp_g; squared-error block sums in
+// part (ceil(m / block) entries)
+int mlp_grad(rhi_ctx* h, const float* X, const float* Y, long long m, double* part) {
+    float *act, *del;
+    int rc;
+    if ((rc = scratch(h, SCR_ACT, (size_t)m * ACT_STRIDE, &act))) return rc;
+    if ((rc = scratch(h, SCR_DEL, (size_t)m * DEL_STRIDE, &del))) return rc;
+    {
+        Scope s(h->prof, "mlp_fwd_bwd");
+        CK(launch_mlp_fwd_bwd(h->mlp_w, X, Y, m, act, del, part, h->st));
+    }
+    {
+        Scope s(h->prof, "mlp_wgrad");
+        CK(launch_mlp_wgrad(act, del, m, h->mlp_g, h->st));
+    }
+    return RHI_OK;
 }
 
 }  // namespace
@@ -532,6 +610,7 @@ int rhi_params_default(rhi_params* p, int n_species) {
     p->u_e = p->u_n = p->u_E = 1.0;
     p->tau = 0.99;
     p->lam_min = 1.0 / 16.0;
+    p->mlp_gate = 1e-3;
     p->growth_max = 1e3;
     p->watchdog = 3;
     p->limiter_jacobian = 0;
@@ -623,6 +702,7 @@ void rhi_destroy(rhi_handle h) {
     if (h->st) cudaStreamSynchronize(h->st);
     else cudaDeviceSynchronize();
     for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
     if (h->h_scal) cudaFreeHost(h->h_scal);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -806,6 +886,8 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
                       double lin_tol) {
     if (!h) return RHI_ERR_ARG;
     if (!h->have_state) return fail(h, RHI_ERR_STATE, "rhi_implicit_step: no state");
+    if (h->prm.guess == RHI_GUESS_LEARNED && !h->mlp_ready)
+        return fail(h, RHI_ERR_STATE, "rhi_implicit_step: learned guess without weights");
     if (!(dt > 0.0) || !(a > 0.0) || !(newton_tol > 0.0) || !(lin_tol > 0.0) || !std::isfinite(adot))
         return fail(h, RHI_ERR_ARG, "rhi_implicit_step: need dt > 0, a > 0, tolerances > 0");
     h->have_linear = false;
@@ -829,10 +911,38 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
     int cur = -1;            // -1: U_k is the state U^n (e_c = 0); 0 / 1: work buffer
     int set = 0;             // Schur set of U_k
     double res = 0.0;
-    if (h->prm.guess == RHI_GUESS_PREVIOUS) {
+    S.guess_used = h->prm.guess;
+    if (h->prm.guess == RHI_GUESS_PREVIOUS || h->prm.guess == RHI_GUESS_LEARNED) {
         B.diag = h->diag[0]; B.rhs = h->rhs[0]; B.fMt = h->fMt[0]; B.MiU = h->MiU[0];
         if ((rc = cell(h, P, MODE_PREP, B))) return rc;
         if ((rc = residual_norm(h, ncell_blocks(h), &res))) return rc;
+        if (h->prm.guess == RHI_GUESS_LEARNED) {
+            // the network's guess into work iterate 1 with its own Schur set; Newton starts
+            // from whichever of U^n and the guess has the smaller ||f||
+            MlpArgs A = mlp_args(h, dt, a);
+            A.U0 = h->U[1];
+            {
+                Scope s(h->prof, "mlp_guess");
+                CK(launch_mlp_infer(A, h->mlp_pk, nullptr, nullptr, 0, 1, h->st));
+            }
+            if ((rc = kappa(h, P, U_n(h, 1), h->kap[1]))) return rc;
+            if ((rc = faces(h, P, U_E(h, 1), h->kap[1], h->W[1], h->PQ[1]))) return rc;
+            PhysBuffers C = state_buffers(h);
+            C.ec = U_ec(h, 1); C.n = U_n(h, 1); C.E = U_E(h, 1); C.W = h->W[1];
+            C.PQ = h->PQ[1]; C.diag_ns = h->diag_ns[1];
+            C.diag = h->diag[1]; C.rhs = h->rhs[1]; C.fMt = h->fMt[1]; C.MiU = h->MiU[1];
+            if ((rc = cell(h, P, MODE_ITER, C))) return rc;
+            double rg = 0.0;
+            if ((rc = residual_norm(h, ncell_blocks(h), &rg))) return rc;
+            S.res_guess_prev = res;
+            if (rg < res) {
+                cur = 1;
+                set = 1;
+                res = rg;
+            } else {
+                S.guess_used = RHI_GUESS_PREVIOUS;
+            }
+        }
     } else {
         B.U0 = h->U[0];
         if ((rc = cell(h, P, MODE_PREP_PREDICT, B))) return rc;
@@ -846,7 +956,6 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
         if ((rc = cell(h, P, MODE_ITER, C))) return rc;
         if ((rc = residual_norm(h, ncell_blocks(h), &res))) return rc;
     }
-    S.guess_used = h->prm.guess;
     S.res_initial = res;
     if (!std::isfinite(res)) { S.status = RHI_ERR_NONPHYSICAL; return fail(h, RHI_ERR_NONPHYSICAL, "non-finite initial residual"); }
 
@@ -947,6 +1056,199 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     S.ms = ms;
     S.launches = h->prof.launches - launches0;
+    h->prof.resolve();
+    return RHI_OK;
+}
+
+// ---- learned guess (an addition to the paper's method)
+
+int rhi_mlp_set_weights(rhi_handle h, const float* w, size_t n) {
+    if (!h) return RHI_ERR_ARG;
+    if (!w || n != (size_t)RHI_MLP_NWEIGHTS)
+        return fail(h, RHI_ERR_ARG, "rhi_mlp_set_weights: need RHI_MLP_NWEIGHTS weights");
+    for (size_t q = 0; q < n; ++q)
+        if (!std::isfinite(w[q])) return fail(h, RHI_ERR_ARG, "rhi_mlp_set_weights: non-finite weight");
+    for (int q = 0; q < RHI_MLP_IN; ++q)
+        if (!(w[n - RHI_MLP_IN + q] > 0.0f)) return fail(h, RHI_ERR_ARG, "rhi_mlp_set_weights: scale must be > 0");
+    int rc = RHI_OK;
+    if (!h->mlp_w) {
+        if (!rc) rc = dalloc(h, &h->mlp_w, n);
+        if (!rc) rc = dalloc(h, &h->mlp_m1, n);
+        if (!rc) rc = dalloc(h, &h->mlp_m2, n);
+        if (!rc) rc = dalloc(h, &h->mlp_g, n);
+        if (!rc) rc = dalloc(h, &h->mlp_pk, 1);
+        if (rc) return rc;
+    }
+    CK(cudaMemcpyAsync(h->mlp_w, w, n * sizeof(float), cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemsetAsync(h->mlp_m1, 0, n * sizeof(float), h->st));
+    CK(cudaMemsetAsync(h->mlp_m2, 0, n * sizeof(float), h->st));
+    CK(cudaMemsetAsync(h->mlp_g, 0, n * sizeof(float), h->st));
+    h->mlp_t = 0;
+    if ((rc = mlp_repack(h))) return rc;
+    h->mlp_ready = true;
+    return RHI_OK;
+}
+
+int rhi_mlp_get_weights(rhi_handle h, float* w, size_t n) {
+    if (!h) return RHI_ERR_ARG;
+    if (!h->mlp_ready) return fail(h, RHI_ERR_STATE, "rhi_mlp_get_weights: no weights set");
+    if (!w || n != (size_t)RHI_MLP_NWEIGHTS)
+        return fail(h, RHI_ERR_ARG, "rhi_mlp_get_weights: need RHI_MLP_NWEIGHTS weights");
+    CK(cudaMemcpyAsync(w, h->mlp_w, n * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return RHI_OK;
+}
+
+int rhi_mlp_features(rhi_handle h, double dt, double a, float* X, int on_device) {
+    if (!h) return RHI_ERR_ARG;
+    if (!h->have_state) return fail(h, RHI_ERR_STATE, "rhi_mlp_features: no state");
+    if (!X || !(dt > 0.0) || !(a > 0.0)) return fail(h, RHI_ERR_ARG, "rhi_mlp_features: bad arguments");
+    const MlpArgs A = mlp_args(h, dt, a);
+    float* dst = X;
+    int rc;
+    if (!on_device && (rc = scratch(h, SCR_X, (size_t)h->N * MLP_IN, &dst))) return rc;
+    {
+        Scope s(h->prof, "mlp_features");
+        CK(launch_mlp_features(A, dst, h->st));
+    }
+    if (!on_device)
+        CK(cudaMemcpyAsync(X, dst, (size_t)h->N * MLP_IN * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->prof.resolve();
+    return RHI_OK;
+}
+
+int rhi_mlp_targets(rhi_handle h, const double* E_old, const double* e_old, const double* n_old,
+                    float* Y, int on_device) {
+    if (!h) return RHI_ERR_ARG;
+    if (!h->have_state) return fail(h, RHI_ERR_STATE, "rhi_mlp_targets: no state");
+    if (!E_old || !e_old || !n_old || !Y) return fail(h, RHI_ERR_ARG, "rhi_mlp_targets: null argument");
+    const long long N = h->N;
+    const double *E0 = E_old, *e0 = e_old, *n0 = n_old;
+    float* dst = Y;
+    int rc;
+    if (!on_device) {
+        // the old state goes through the second work iterate (E | e | n), nv * N doubles
+        double* b = h->U[1];
+        CK(cudaMemcpyAsync(b, E_old, N * sizeof(double), cudaMemcpyHostToDevice, h->st));
+        CK(cudaMemcpyAsync(b + N, e_old, N * sizeof(double), cudaMemcpyHostToDevice, h->st));
+        CK(cudaMemcpyAsync(b + 2 * N, n_old, (size_t)h->ns * N * sizeof(double), cudaMemcpyHostToDevice, h->st));
+        E0 = b; e0 = b + N; n0 = b + 2 * N;
+        if ((rc = scratch(h, SCR_Y, (size_t)N * MLP_OUT, &dst))) return rc;
+        h->have_linear = false;
+    }
+    const MlpArgs A = mlp_args(h, 1.0, 1.0);
+    {
+        Scope s(h->prof, "mlp_targets");
+        CK(launch_mlp_targets(A, E0, e0, n0, dst, h->st));
+    }
+    if (!on_device)
+        CK(cudaMemcpyAsync(Y, dst, (size_t)N * MLP_OUT * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->prof.resolve();
+    return RHI_OK;
+}
+
+int rhi_mlp_forward(rhi_handle h, const float* X, float* Y, long long n, int on_device) {
+    if (!h) return RHI_ERR_ARG;
+    if (!h->mlp_ready) return fail(h, RHI_ERR_STATE, "rhi_mlp_forward: no weights set");
+    if (!X || !Y || n < 0) return fail(h, RHI_ERR_ARG, "rhi_mlp_forward: bad arguments");
+    if (n == 0) return RHI_OK;
+    const float* src = X;
+    float* dst = Y;
+    int rc;
+    if (!on_device) {
+        float *xs, *ys;
+        if ((rc = scratch(h, SCR_X, (size_t)n * MLP_IN, &xs))) return rc;
+        if ((rc = scratch(h, SCR_Y, (size_t)n * MLP_OUT, &ys))) return rc;
+        CK(cudaMemcpyAsync(xs, X, (size_t)n * MLP_IN * sizeof(float), cudaMemcpyHostToDevice, h->st));
+        src = xs;
+        dst = ys;
+    }
+    MlpArgs A{};
+    {
+        Scope s(h->prof, "mlp_infer");
+        CK(launch_mlp_infer(A, h->mlp_pk, src, dst, n, 0, h->st));
+    }
+    if (!on_device)
+        CK(cudaMemcpyAsync(Y, dst, (size_t)n * MLP_OUT * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->prof.resolve();
+    return RHI_OK;
+}
+
+int rhi_mlp_loss_grad(rhi_handle h, const float* X, const float* Y, long long n, float* grad,
+                      double* loss, int on_device) {
+    if (!h) return RHI_ERR_ARG;
+    if (!h->mlp_ready) return fail(h, RHI_ERR_STATE, "rhi_mlp_loss_grad: no weights set");
+    if (!X || !Y || n < 1) return fail(h, RHI_ERR_ARG, "rhi_mlp_loss_grad: bad arguments");
+    const float *xs = X, *ys = Y;
+    int rc;
+    if (!on_device) {
+        float *xd, *yd;
+        if ((rc = scratch(h, SCR_X, (size_t)n * MLP_IN, &xd))) return rc;
+        if ((rc = scratch(h, SCR_Y, (size_t)n * MLP_OUT, &yd))) return rc;
+        CK(cudaMemcpyAsync(xd, X, (size_t)n * MLP_IN * sizeof(float), cudaMemcpyHostToDevice, h->st));
+        CK(cudaMemcpyAsync(yd, Y, (size_t)n * MLP_OUT * sizeof(float), cudaMemcpyHostToDevice, h->st));
+        xs = xd;
+        ys = yd;
+    }
+    const long long nb = (n + mlp_train_block() - 1) / mlp_train_block();
+    double* part;
+    if ((rc = scratch(h, SCR_PART, (size_t)nb, &part))) return rc;
+    CK(cudaMemsetAsync(h->mlp_g, 0, RHI_MLP_NWEIGHTS * sizeof(float), h->st));
+    if ((rc = mlp_grad(h, xs, ys, n, part))) return rc;
+    LinLaunch L(h->st, &h->prof);
+    CK(L.reduce(part, (int)nb, h->scal, RED_SUM, S_TMP));
+    double se = 0.0;
+    if ((rc = read_scalar(h, S_TMP, &se))) return rc;
+    if (loss) *loss = se / ((double)n * MLP_OUT);
+    if (grad)
+        CK(cudaMemcpyAsync(grad, h->mlp_g, RHI_MLP_NWEIGHTS * sizeof(float),
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->prof.resolve();
+    return RHI_OK;
+}
+
+int rhi_mlp_train(rhi_handle h, const float* X, const float* Y, long long n, int epochs,
+                  int batch, double lr, double* loss) {
+    if (!h) return RHI_ERR_ARG;
+    if (!h->mlp_ready) return fail(h, RHI_ERR_STATE, "rhi_mlp_train: no weights set");
+    if (!X || !Y || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0))
+        return fail(h, RHI_ERR_ARG, "rhi_mlp_train: bad arguments");
+    const long long tb = mlp_train_block();
+    const long long nbatch = (n + batch - 1) / batch;
+    // block partials of one epoch, one slice per minibatch
+    const long long nparts = nbatch * (((long long)batch + tb - 1) / tb);
+    if (nparts > (1LL << 30)) return fail(h, RHI_ERR_ARG, "rhi_mlp_train: too many samples");
+    double* part;
+    int rc;
+    if ((rc = scratch(h, SCR_PART, (size_t)nparts, &part))) return rc;
+    CK(cudaMemsetAsync(part, 0, (size_t)nparts * sizeof(double), h->st));
+    const int nupd = RHI_MLP_NWEIGHTS - 2 * RHI_MLP_IN;        // normalisation stays fixed
+    for (int ep = 0; ep < epochs; ++ep) {
+        long long po = 0;
+        for (long long b = 0; b < nbatch; ++b) {
+            const long long s0 = b * batch;
+            const long long m = std::min<long long>(batch, n - s0);
+            if ((rc = mlp_grad(h, X + s0 * MLP_IN, Y + s0 * MLP_OUT, m, part + po))) return rc;
+            po += (m + tb - 1) / tb;
+            h->mlp_t += 1;
+            const float b1t = (float)std::pow(0.9, (double)h->mlp_t);
+            const float b2t = (float)std::pow(0.999, (double)h->mlp_t);
+            Scope s(h->prof, "mlp_adam");
+            CK(launch_mlp_adam(h->mlp_w, h->mlp_g, h->mlp_m1, h->mlp_m2, nupd, (float)lr, b1t, b2t, h->st));
+        }
+        if (ep == epochs - 1 && loss) {
+            LinLaunch L(h->st, &h->prof);
+            CK(L.reduce(part, (int)po, h->scal, RED_SUM, S_TMP));
+            double se = 0.0;
+            if ((rc = read_scalar(h, S_TMP, &se))) return rc;
+            *loss = se / ((double)n * MLP_OUT);
+        }
+    }
+    if ((rc = mlp_repack(h))) return rc;
     h->prof.resolve();
     return RHI_OK;
 }

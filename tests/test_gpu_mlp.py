@@ -1,0 +1,208 @@
+"""Learned Newton initial guess: the CUDA kernels (features, targets, BF16 tensor-core forward,
+FP32 backward, Adam) vs the FP64 oracle in oracle/mlp.py, and the guess inside the implicit
+step (same root as the oracle's Newton solution, fewer Newton iterations once trained)."""
+import numpy as np
+import pytest
+
+from conftest import oracle_problem
+from oracle import mlp as om, solve as sv
+from paper_0901_1110_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+KPC = inputs.KPC
+
+
+@pytest.fixture(scope="module")
+def rhi():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_0901_1110_gb300 import _build
+    _build.build()
+    import paper_0901_1110_gb300 as rhi
+    rhi.lib()
+    return rhi
+
+
+def _workload(seed, shape=(20, 22, 24), nsteps=4):
+    w = inputs.lognormal_hhe(shape, box=200 * KPC, nsrc=3, dt=5e12, nsteps=nsteps, seed=seed)
+    w.theta = 1.0
+    w.u_E = 1e-18
+    return w
+
+
+def _flat_state(st):
+    return dict(E=np.ascontiguousarray(st["E"]).ravel(), e=np.ascontiguousarray(st["e"]).ravel(),
+                n=np.ascontiguousarray(st["n"]).ravel())
+
+
+def _normalised(w, X):
+    """Weights with the input normalisation set from the training features."""
+    d = om.unpack(w)
+    d["mean"] = X.mean(axis=0)
+    sd = X.std(axis=0)
+    d["scale"] = np.where(sd > 1e-3, sd, 1.0)
+    return om.pack(d)
+
+
+def _trajectory(s, w, nsteps):
+    """Features at U^n and targets of U^n -> U^{n+1} along nsteps GPU steps."""
+    Xs, Ys = [], []
+    for _ in range(nsteps):
+        old = _flat_state(s.get_state())
+        Xs.append(s.mlp_features(w.dt))
+        s.step(w.dt, newton_tol=1e-10, lin_tol=1e-10)
+        Ys.append(s.mlp_targets(old))
+    return np.concatenate(Xs), np.concatenate(Ys)
+
+
+@pytest.fixture(scope="module")
+def trained(rhi):
+    """A network trained on the GPU on a 4-step trajectory of seed 11."""
+    import torch
+    w = _workload(11)
+    s = rhi.solver_for_workload(w, precond=rhi.RHI_PRECOND_MG_FP32, mg_levels=4)
+    X, Y = _trajectory(s, w, w.nsteps)
+    w0 = _normalised(om.init_weights(3), X).astype(np.float32)
+    s.mlp_set_weights(w0)
+    Xd = torch.from_numpy(X).cuda()
+    Yd = torch.from_numpy(Y).cuda()
+    losses = [s.mlp_train(Xd, Yd, epochs=1, batch=512, lr=2e-3)]
+    for _ in range(5):
+        losses.append(s.mlp_train(Xd, Yd, epochs=8, batch=512, lr=2e-3))
+    return dict(w=s.mlp_get_weights(), X=X, Y=Y, losses=losses, workload=w)
+
+
+def test_features_and_targets_match_oracle(rhi):
+    """Features of the state at t^n and targets of one step (FP32 kernels from the FP64
+    state) vs the oracle's FP64 definitions, element by element."""
+    w = _workload(5)
+    s = rhi.solver_for_workload(w)
+    p = oracle_problem(w)
+    st0 = w.state()
+    X = s.mlp_features(w.dt, a=0.7)
+    Xr = om.features(p, st0, w.dt, a=0.7)
+    np.testing.assert_allclose(X, Xr, rtol=2e-6, atol=2e-5)
+    old = _flat_state(s.get_state())
+    s.step(w.dt, newton_tol=1e-10, lin_tol=1e-10)
+    Y = s.mlp_targets(old)
+    new = s.get_state()
+    Yr = om.targets(p, dict(E=old["E"], e=old["e"], n=old["n"].reshape(w.ns, -1)), new)
+    np.testing.assert_allclose(Y, Yr, rtol=2e-6, atol=2e-5)
+
+
+def test_tensor_core_forward_matches_oracle(rhi):
+    """BF16 weights and activations with FP32 accumulation vs the FP64 forward pass: each
+    layer rounds its inputs and weights to 8 significant bits (relative 2^-9), so the output
+    error stays at the percent level of the output scale; ragged row counts and the
+    64-row tiles both covered."""
+    rng = np.random.default_rng(0)
+    w = _normalised(om.init_weights(7), rng.standard_normal((256, 9)) * 3 + 1)
+    s = rhi.Solver(2, 2, 2, 1.0, rhi.rhi_params_default(1))
+    s.mlp_set_weights(w.astype(np.float32))
+    w32 = s.mlp_get_weights()
+    assert np.array_equal(w32, w.astype(np.float32))
+    for n in (1, 31, 33, 1000, 4099):
+        X = (rng.standard_normal((n, 9)) * 3 + 1).astype(np.float32)
+        Y = s.mlp_forward(X)
+        Yr = om.forward(w32.astype(np.float64), X.astype(np.float64))
+        scale = max(1.0, float(np.abs(Yr).max()))
+        err = np.abs(Y - Yr)
+        assert err.max() <= 3e-2 * scale, (n, err.max(), scale)
+        assert np.median(err) <= 5e-3 * scale
+    s.close()
+
+
+def test_gradient_matches_oracle(rhi):
+    """FP32 per-sample backward + deterministic weight-gradient reduction vs the FP64 oracle
+    gradient (normwise 1e-4) and loss (1e-5), with a ragged sample count."""
+    rng = np.random.default_rng(1)
+    w = _normalised(om.init_weights(2), rng.standard_normal((64, 9)))
+    w32 = w.astype(np.float32)
+    s = rhi.Solver(2, 2, 2, 1.0, rhi.rhi_params_default(1))
+    s.mlp_set_weights(w32)
+    for n in (1, 200, 3001):
+        X = rng.standard_normal((n, 9)).astype(np.float32)
+        Y = rng.standard_normal((n, 6)).astype(np.float32)
+        loss, g = s.mlp_loss_grad(X, Y)
+        lr, gr = om.loss_and_grad(w32.astype(np.float64), X.astype(np.float64), Y.astype(np.float64))
+        assert abs(loss / lr - 1) < 1e-5
+        assert np.linalg.norm(g - gr) <= 1e-4 * np.linalg.norm(gr), n
+        assert np.all(g[-18:] == 0)
+    s.close()
+
+
+def test_training_reduces_loss_and_is_deterministic(rhi, trained):
+    """Adam on the GPU lowers the loss of the trajectory data by a large factor, and two runs
+    from the same weights on the same data give identical weights."""
+    import torch
+    L = trained["losses"]
+    assert L[-1] < 0.1 * L[0], L
+    X, Y = trained["X"][:3000], trained["Y"][:3000]
+    w0 = _normalised(om.init_weights(4), X).astype(np.float32)
+    outs = []
+    for _ in range(2):
+        s = rhi.Solver(2, 2, 2, 1.0, rhi.rhi_params_default(3))
+        s.mlp_set_weights(w0)
+        s.mlp_train(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), epochs=2, batch=256,
+                    lr=1e-3)
+        outs.append(s.mlp_get_weights())
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
+    # the GPU loss of the trained weights agrees with the oracle's
+    lr_, _ = om.loss_and_grad(outs[0].astype(np.float64), X.astype(np.float64), Y.astype(np.float64))
+    s = rhi.Solver(2, 2, 2, 1.0, rhi.rhi_params_default(3))
+    s.mlp_set_weights(outs[0])
+    lg, _ = s.mlp_loss_grad(X, Y)
+    assert abs(lg / lr_ - 1) < 1e-5
+
+
+def test_learned_guess_reaches_the_same_root(rhi, trained):
+    """The implicit step started from the network's guess converges to the oracle's Newton
+    solution (started from U^n, exact linear solves)."""
+    w = trained["workload"]
+    s = rhi.solver_for_workload(w, guess=rhi.RHI_GUESS_LEARNED)
+    s.mlp_set_weights(trained["w"])
+    p = oracle_problem(w)
+    ref = w.state()
+    used = []
+    for _ in range(2):
+        s.step(w.dt, newton_tol=1e-12, lin_tol=1e-12)
+        st = s.stats()
+        used.append(st["guess_used"])
+        assert st["res_guess_prev"] > 0
+        ref, info = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, 1e-13, linear="direct")
+        assert info["converged"]
+        g = s.get_state()
+        for key in ("E", "e", "n"):
+            a = np.asarray(g[key]).reshape(np.shape(ref[key]))
+            assert np.abs(a - ref[key]).max() <= 1e-10 * np.abs(ref[key]).max(), key
+    assert rhi.RHI_GUESS_LEARNED in used, used
+
+
+def test_learned_guess_needs_weights(rhi):
+    w = _workload(5, shape=(4, 4, 4))
+    s = rhi.solver_for_workload(w, guess=rhi.RHI_GUESS_LEARNED)
+    with pytest.raises(rhi.RhiError):
+        s.step(w.dt)
+    with pytest.raises(rhi.RhiError):
+        s.mlp_set_weights(np.zeros(10, dtype=np.float32))
+    bad = np.zeros(rhi.RHI_MLP_NWEIGHTS, dtype=np.float32)       # scale 0
+    with pytest.raises(rhi.RhiError):
+        s.mlp_set_weights(bad)
+
+
+def test_learned_guess_lowers_newton_iterations(rhi, trained):
+    """On a held-out realisation (another seed of the same workload family), the trained guess
+    needs fewer Newton iterations over the trajectory than starting from U^n."""
+    w = _workload(23)
+    its = {}
+    for guess in (rhi.RHI_GUESS_PREVIOUS, rhi.RHI_GUESS_LEARNED):
+        s = rhi.solver_for_workload(w, guess=guess, precond=rhi.RHI_PRECOND_MG_FP32, mg_levels=4)
+        if guess == rhi.RHI_GUESS_LEARNED:
+            s.mlp_set_weights(trained["w"])
+        n = 0
+        for _ in range(w.nsteps):
+            s.step(w.dt, newton_tol=1e-10, lin_tol=1e-10)
+            n += s.stats()["newton_its"]
+        its[guess] = n
+    assert its[rhi.RHI_GUESS_LEARNED] < its[rhi.RHI_GUESS_PREVIOUS], its
