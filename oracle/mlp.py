@@ -148,9 +148,19 @@ def loss_and_grad(w, X, Y):
     return loss, pack(grads)
 
 
-def decode(p, state, out, gate=0.0):
+def out_of_distribution(w, X, ood):
+    """Cells whose normalised features (X - mean) / scale leave [-ood, ood] in any component:
+    the network has seen too few such cells to be trusted there (ood <= 0: none)."""
+    if ood is None or ood <= 0:
+        return np.zeros(X.shape[0], dtype=bool)
+    d = unpack(w)
+    return np.any(np.abs((X - d["mean"]) / d["scale"]) > ood, axis=1)
+
+
+def decode(p, state, out, gate=0.0, ood_mask=None):
     """Predicted state (E, e, n) from network outputs; cells whose predicted changes are all
-    below ``gate`` (in log10 / logit units) keep the old state."""
+    below ``gate`` (in log10 / logit units), and cells flagged in ``ood_mask``, keep the old
+    state."""
     E0 = np.asarray(state["E"]).ravel()
     e0 = np.asarray(state["e"]).ravel()
     n0 = np.asarray(state["n"]).reshape(p.ns, -1)
@@ -173,6 +183,8 @@ def decode(p, state, out, gate=0.0):
         dlog = np.abs(np.log(np.maximum(f, FLOOR)) - np.log(np.maximum(f0, FLOOR)))
         change = np.maximum(change, dlog.max(axis=1))
     keep = change < gate
+    if ood_mask is not None:
+        keep = keep | ood_mask
     E = np.where(keep, E0, E)
     e = np.where(keep, e0, e)
     n = np.where(keep[None, :], n0, n)

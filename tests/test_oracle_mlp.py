@@ -61,3 +61,30 @@ def test_features_of_a_known_cell():
     np.testing.assert_allclose(X[:, 2], np.log10(0.75), rtol=1e-15)
     np.testing.assert_allclose(X[:, 5], 0.0, atol=1e-15)
     np.testing.assert_allclose(X[:, 8], 0.0, atol=1e-15)
+
+
+def test_out_of_distribution_cells_keep_the_old_state():
+    """A feature 7 scales from the training mean flags its cell; flagged cells decode to the
+    old state whatever the outputs, the others follow the outputs."""
+    w = inputs.lognormal_hhe((4, 4, 4), nsrc=1)
+    p = oracle_problem(w)
+    st = w.state()
+    X = mlp.features(p, st, 5e12)
+    d = mlp.unpack(mlp.init_weights(0))
+    d["mean"] = X.mean(axis=0)
+    d["scale"] = np.ones(mlp.NIN)
+    wts = mlp.pack(d)
+    Xo = X.copy()
+    Xo[5, 3] = d["mean"][3] + 7.0
+    Xo[9, 0] = d["mean"][0] - 7.0
+    mask = mlp.out_of_distribution(wts, Xo, 6.0)
+    expected = mlp.out_of_distribution(wts, X, 6.0)
+    expected[[5, 9]] = True
+    np.testing.assert_array_equal(mask, expected)
+    assert not mlp.out_of_distribution(wts, Xo, 0.0).any()
+    Y = mlp.targets(p, st, st)
+    Y[:, 0] += 0.5                                  # every cell predicts E x 10^0.5
+    out = mlp.decode(p, st, Y, gate=0.0, ood_mask=mask)
+    E0 = np.asarray(st["E"]).ravel()
+    np.testing.assert_array_equal(out["E"][mask], E0[mask])
+    np.testing.assert_allclose(out["E"][~mask], E0[~mask] * 10 ** 0.5, rtol=1e-14)
