@@ -3,10 +3,12 @@
 One bench step = one rhi_implicit_step (g^n, Newton iterations with the fused residual /
 Jacobian / Schur kernel, multigrid-preconditioned CG on the Schur system, recovery and
 positivity-limited update) over the 256^3 hydrogen + helium lognormal workload (64 lognormal
-point sources, T_B = 1e5 K blackbody, 5e12 s steps, Newton tol 1e-8, PCG tol 1e-10).  The
-headline form runs the FP32 multigrid preconditioner inside FP64 CG; the plain FP64 form is
-timed beside it on the same workload.  Inputs (about 8 GB of fields per form) exceed the
-129 MB L2, so no flush is needed between steps.
+point sources, T_B = 1e5 K blackbody, 5e12 s steps, Newton tol 1e-8, PCG tol 1e-10).  Three
+forms run on the same workload: plain FP64 (FP64 multigrid), mixed (FP32 multigrid inside
+FP64 CG) and, as the headline, learned + mixed (the mixed form started from the learned
+Newton guess, trained on the GPU beforehand from 128^3 runs; training time is reported, not
+timed).  Inputs (about 8 GB of fields per form) exceed the 129 MB L2, so no flush is needed
+between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--n 256]
 Under torchrun each rank runs its own replica (independent problem, different seed).
@@ -40,6 +42,26 @@ def load_peaks():
 # FP64 peak of the CUDA cores derived from the unit counts: 152 SMs x 2070 MHz x 2 DFMA/clk/SM
 # x 2 flop = 1.259 TFLOP/s (a register-resident DFMA loop measures 1.20 TFLOP/s)
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
+
+# FP64 flops per cell of the fused cell kernels (bound by the FP64 pipe, about 1.2 TFLOP/s here),
+# counted by ncu as 2 DFMA + DMUL + DADD thread instructions per cell
+ALU_FLOPS = {
+    "cell_residual_schur": 585,
+}
+# DRAM bytes per launch (read + write) from ncu, scaled to the 256^3 workload; None once the
+# kernel has changed since the counters were taken
+TRAFFIC = {}
+# launches bracketed by events inside the timed region
+TIMED_KERNELS = ["cell_residual_schur"]
+
+FORM_TEXT = {
+    "plain_fp64": "FP64 Newton/Schur/CG + FP64 multigrid V-cycle (6 levels, 2+2 Jacobi, 16 "
+                  "coarse sweeps), Newton from U^n",
+    "mixed_fp32mg": "FP64 Newton/Schur/CG + FP32 multigrid V-cycle (6 levels, 2+2 Jacobi, 16 "
+                    "coarse sweeps), Newton from U^n",
+    "learned_mixed": "mixed form + learned Newton guess (BF16 tensor-core MLP 9-64-64-64-6, "
+                     "falls back to U^n when its ||f|| is larger)",
+}
 
 # algorithmic DRAM bytes per cell of each kernel (H + He; FP64 fields 8 B): the fields each
 # launch must read and write once; stencil neighbours come from cache
@@ -176,47 +198,121 @@ def cpu_baseline_sample():
                       "(numpy/scipy; BLAS threads over the host cores)"}
 
 
-def run_form(rhi, w, torch, steps, warmup, precond, profile, limiter_jacobian=0,
-             max_newton=200):
-    """Times `steps` implicit steps after `warmup` with CUDA events on the library's stream."""
+def run_form(rhi, w, torch, steps, warmup, precond, time_names, limiter_jacobian=0,
+             max_newton=200, guess=0, weights=None):
+    """Times `steps` implicit steps after `warmup` with CUDA events on the library's stream.
+    Inside the timed region only the launches named in `time_names` are bracketed by events
+    (their per-launch device time gives the roofline); one further step after the timed
+    region brackets every launch for the per-kernel breakdown."""
     stream = torch.cuda.Stream()
     s = rhi.solver_for_workload(w, stream=stream.cuda_stream, precond=precond, mg_levels=6,
                                 theta=1.0, limiter_jacobian=limiter_jacobian,
-                                max_newton=max_newton)
+                                max_newton=max_newton, guess=guess)
+    if weights is not None:
+        s.mlp_set_weights(weights)
     for _ in range(warmup):
         rc = s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol, check=False)
         if rc:
             st = s.stats()
             raise RuntimeError(f"warm-up step failed ({rc}): newton_its={st['newton_its']} "
                                f"residuals={st['res_history']}")
-    s.set_profiling(profile)
+    s.set_profiling(True, names=time_names)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    agg = dict(newton_its=0, pcg_its=0, vcycles=0, launches=0, backtracks=0)
+    agg = dict(newton_its=0, pcg_its=0, vcycles=0, launches=0, backtracks=0, learned_used=0,
+               guess_restarts=0)
     e0.record(stream)
-    hist = []
+    hist, res0, prev0 = [], [], []
     for _ in range(steps):
         s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol)
         st = s.stats()
         for k in agg:
-            agg[k] += st[k]
+            if k in st:
+                agg[k] += st[k]
+        agg["learned_used"] += int(st["guess_used"] == rhi.RHI_GUESS_LEARNED)
         hist.append(st["res_history"])
-    agg["res_history_last"] = hist[-1]
+        res0.append(st["res_initial"])
+        prev0.append(st["res_guess_prev"])
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    kt = s.kernel_times() if profile else {}
+    kt_timed = s.kernel_times()
+    agg["res_history_last"] = hist[-1]
+    agg["res_initial"] = res0
+    agg["res_prev_guess"] = prev0
+    # per-kernel breakdown of one more step, every launch bracketed (not part of the timing)
+    s.set_profiling(True)
+    s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol)
+    kt_all = s.kernel_times()
     s.set_profiling(False)
-    return s, ms, agg, kt
+    return s, ms, agg, kt_timed, kt_all
 
 
-def e2e_form(rhi, w, torch, steps, warmup, precond, limiter_jacobian=0, max_newton=200):
+def train_guess(rhi, torch, rank, train_steps, epochs):
+    """Trains the learned guess on the GPU from Newton solutions of 128^3 lognormal runs
+    (16 sources in 1 Mpc, seeds distinct from the timed workload's), mixed form."""
+    from paper_0901_1110_gb300 import inputs
+    t0 = time.perf_counter()
+    w = inputs.config_lognormal(128, nsrc=16, seed=1000 + rank)
+    s = rhi.solver_for_workload(w, precond=rhi.RHI_PRECOND_MG_FP32, mg_levels=6, theta=1.0,
+                                max_newton=200)
+    N = w.N
+    X = torch.empty((train_steps * N, rhi.RHI_MLP_IN), dtype=torch.float32, device="cuda")
+    Y = torch.empty((train_steps * N, rhi.RHI_MLP_OUT), dtype=torch.float32, device="cuda")
+    old = {k: torch.empty(m * N, dtype=torch.float64, device="cuda")
+           for k, m in (("E", 1), ("e", 1), ("n", w.ns))}
+    for k in range(train_steps):
+        s.get_state(old["E"], old["e"], old["n"])
+        s.mlp_features(w.dt, out=X[k * N:(k + 1) * N])
+        s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol)
+        s.mlp_targets(old, out=Y[k * N:(k + 1) * N])
+    t_data = time.perf_counter() - t0
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    perm = torch.randperm(X.shape[0], device="cuda", generator=g)
+    X = X[perm].contiguous()
+    Y = Y[perm].contiguous()
+    mean = X.mean(dim=0)
+    sd = X.std(dim=0)
+    sd = torch.where(sd > 1e-3, sd, torch.ones_like(sd))
+    w0 = init_weights(rhi, mean.cpu().numpy(), sd.cpu().numpy())
+    s.mlp_set_weights(w0)
+    losses = []
+    for ep in range(epochs):
+        lr = 2e-3 if ep < epochs - 1 else 5e-4
+        losses.append(s.mlp_train(X, Y, epochs=1, batch=4096, lr=lr))
+    torch.cuda.synchronize()
+    wts = s.mlp_get_weights()
+    s.close()
+    info = {"samples": int(X.shape[0]), "epochs": epochs, "loss_per_epoch": losses,
+            "data_s": t_data, "total_s": time.perf_counter() - t0,
+            "source": f"{train_steps} steps of lognormal_hhe 128^3, 16 sources, 1 Mpc, seed {1000 + rank}"}
+    return wts, info
+
+
+def init_weights(rhi, mean, scale, seed=0):
+    """He-initialised weights in the library's layout with the given input normalisation."""
+    rng = np.random.default_rng(seed)
+    I, H, O = rhi.RHI_MLP_IN, rhi.RHI_MLP_HID, rhi.RHI_MLP_OUT
+    parts = []
+    for rows, cols in ((H, I), (H, H), (H, H), (O, H)):
+        parts.append(rng.standard_normal(rows * cols) * np.sqrt(2.0 / cols))
+        parts.append(np.zeros(rows))
+    parts += [np.asarray(mean, dtype=np.float64), np.asarray(scale, dtype=np.float64)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def e2e_form(rhi, w, torch, steps, warmup, precond, limiter_jacobian=0, max_newton=200,
+             guess=0, weights=None):
     """Same metric through the public API with host buffers: each timed step copies the
     step's inputs (E, e, n, n_H and the point-source list) from pinned host memory, runs the
     step and reads the state (E, e, n) back into pinned host memory."""
     s = rhi.solver_for_workload(w, precond=precond, mg_levels=6, theta=1.0,
-                                limiter_jacobian=limiter_jacobian, max_newton=max_newton)
+                                limiter_jacobian=limiter_jacobian, max_newton=max_newton,
+                                guess=guess)
+    if weights is not None:
+        s.mlp_set_weights(weights)
     N = w.N
     pin = lambda m: torch.empty(m, dtype=torch.float64, pin_memory=True).numpy()
     st = w.state()
@@ -253,8 +349,11 @@ def main():
     ap.add_argument("--impl", default="rhi")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="plain_fp64,mixed_fp32mg",
+    ap.add_argument("--forms", default="plain_fp64,mixed_fp32mg,learned_mixed",
                     help="comma list of forms to time (the last one is the headline)")
+    ap.add_argument("--train-steps", type=int, default=20,
+                    help="steps of the 128^3 training run for the learned guess")
+    ap.add_argument("--train-epochs", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--max-newton", type=int, default=200)
     ap.add_argument("--limiter-jacobian", type=int, default=0,
@@ -287,25 +386,33 @@ def main():
     w = inputs.config_lognormal(n, nsrc=nsrc, seed=rank)
     hbm_peak, peak_src = load_peaks()
 
-    # plain FP64 form (FP64 multigrid), then the mixed form (FP32 multigrid) as headline
-    forms = {}
-    codes = {"plain_fp64": rhi.RHI_PRECOND_MG_FP64, "mixed_fp32mg": rhi.RHI_PRECOND_MG_FP32}
-    ljac = {"plain_fp64": args.limiter_jacobian, "mixed_fp32mg": args.limiter_jacobian}
+    # forms: plain FP64 (FP64 multigrid), mixed (FP32 multigrid), learned + mixed (headline)
+    FORMS = {"plain_fp64": (rhi.RHI_PRECOND_MG_FP64, rhi.RHI_GUESS_PREVIOUS),
+             "mixed_fp32mg": (rhi.RHI_PRECOND_MG_FP32, rhi.RHI_GUESS_PREVIOUS),
+             "learned_mixed": (rhi.RHI_PRECOND_MG_FP32, rhi.RHI_GUESS_LEARNED)}
     order = [f for f in args.forms.split(",") if f]
+    weights, train_info = None, None
+    if any(FORMS[f][1] == rhi.RHI_GUESS_LEARNED for f in order):
+        weights, train_info = train_guess(rhi, torch, rank, args.train_steps, args.train_epochs)
+        torch.cuda.empty_cache()
+    forms = {}
     for name in order:
-        pc = codes[name]
+        pc, guess = FORMS[name]
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         clk = ClockSampler(local)
         clk.start()
-        s, ms, agg, kt = run_form(rhi, w, torch, args.steps, args.warmup, pc, profile=True,
-                                  limiter_jacobian=ljac[name], max_newton=args.max_newton)
+        s, ms, agg, kt_timed, kt_all = run_form(
+            rhi, w, torch, args.steps, args.warmup, pc, TIMED_KERNELS,
+            limiter_jacobian=args.limiter_jacobian, max_newton=args.max_newton, guess=guess,
+            weights=weights if guess == rhi.RHI_GUESS_LEARNED else None)
         clocks = clk.stop()
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         if dist:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        forms[name] = dict(ms=float(t.item()), agg=agg, kt=kt, clocks=clocks)
+        forms[name] = dict(ms=float(t.item()), agg=agg, kt=kt_all, kt_timed=kt_timed,
+                           clocks=clocks)
         s.close()
         del s
         torch.cuda.empty_cache()
@@ -314,16 +421,28 @@ def main():
     ms_step = head["ms"] / args.steps
     value = world * w.N * args.steps / (head["ms"] * 1e-3)
 
-    # dominant kernel and its roofline
+    # dominant kernel (largest share of the breakdown step) and its roofline from the
+    # per-launch device times inside the timed region
     kt = head["kt"]
     tot = sum(v[0] for v in kt.values())
-    tname, (tms, tcnt) = max(kt.items(), key=lambda kv: kv[1][0])
-    avg_s = tms / tcnt * 1e-3
-    roof = {"kernel": tname, "share": tms / tot if tot else None, "avg_launch_ms": avg_s * 1e3}
-    if tname in ALG_BYTES:
-        ach = ALG_BYTES[tname] * w.N / avg_s / 1e9
-        roof.update(bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak,
-                    traffic=None, peak_source=peak_src)
+    tname = max(kt.items(), key=lambda kv: kv[1][0])[0]
+    roof = {"kernel": tname, "share": kt[tname][0] / tot if tot else None}
+    if tname in head["kt_timed"]:
+        tms, tcnt = head["kt_timed"][tname]
+        avg_s = tms / tcnt * 1e-3
+        roof["avg_launch_ms"] = avg_s * 1e3
+        roof["launches_timed"] = tcnt
+        if tname in ALU_FLOPS:
+            ach = ALU_FLOPS[tname] * w.N / avg_s / 1e12
+            roof.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                        frac=ach / FP64_PEAK_TFLOPS, traffic=TRAFFIC.get(tname),
+                        flops_per_cell=ALU_FLOPS[tname],
+                        peak_source="derived: 152 SMs x 2070 MHz x 2 DFMA/clk/SM x 2 flop")
+        elif tname in ALG_BYTES:
+            ach = ALG_BYTES[tname] * w.N / avg_s / 1e9
+            roof.update(bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s",
+                        frac=ach / hbm_peak, traffic=TRAFFIC.get(tname),
+                        peak_source=peak_src)
     # HBM fraction of the FP64 CG stencil / vector kernels (one full-grid launch each)
     lin = {}
     for k in ("cg_matvec_dot", "cg_update_xr", "cg_update_p"):
@@ -331,7 +450,14 @@ def main():
             ms_k, c_k = kt[k]
             lin[k] = ALG_BYTES[k] * w.N / (ms_k / c_k * 1e-3) / 1e9 / hbm_peak
 
-    plain = forms.get("plain_fp64", head)
+    def summary(f):
+        return {"value": world * w.N * args.steps / (f["ms"] * 1e-3),
+                "ms_per_step": f["ms"] / args.steps,
+                **{k: v / args.steps for k, v in f["agg"].items()
+                   if isinstance(v, (int, float))},
+                "kernel_ms_breakdown_step": {k: v[0] for k, v in
+                                             sorted(f["kt"].items(), key=lambda kv: -kv[1][0])}}
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -339,31 +465,28 @@ def main():
         "config": {"workload": f"lognormal_hhe {n}^3 H+He, sigma_ln=1, P(k)~k^-2, {nsrc} sources "
                                "(median 1e49/s), T_B=1e5 K, dt=5e12 s, theta=1, Newton tol "
                                "1e-8 (u_E = 1e-16), PCG tol 1e-10",
-                   "form": "FP64 Newton/Schur/CG + FP32 multigrid V-cycle (6 levels, 2+2 "
-                           "Jacobi, 16 coarse sweeps)",
+                   "form": FORM_TEXT[order[-1]],
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (~8 GB of fields per form)"},
         "roofline": roof,
-        "plain_fp64": {"value": world * w.N * args.steps / (plain["ms"] * 1e-3),
-                       "ms_per_step": plain["ms"] / args.steps,
-                       **{k: v / args.steps for k, v in plain["agg"].items()
-                          if k != "res_history_last"}},
+        "forms": {k: summary(f) for k, f in forms.items()},
         "iterations_per_step": {k: v / args.steps for k, v in head["agg"].items()
-                                if k != "res_history_last"},
+                                if isinstance(v, (int, float))},
         "newton_residuals_last_step": head["agg"]["res_history_last"],
         "gpu_launches": head["agg"]["launches"],
         "clocks": head["clocks"],
-        "kernel_ms_per_step": {k: v[0] / args.steps
-                               for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])},
-        "plain_kernel_ms_per_step": {k: v[0] / args.steps
-                                     for k, v in sorted(plain["kt"].items(),
-                                                        key=lambda kv: -kv[1][0])},
         "hbm_frac_linear_kernels": lin,
     }
+    if "plain_fp64" in forms and order[-1] != "plain_fp64":
+        line["speedup_vs_plain_fp64"] = forms["plain_fp64"]["ms"] / head["ms"]
+    if train_info:
+        line["learned_guess_training"] = train_info
     if rank == 0:
         if not args.no_e2e:
-            e2e_val, h2d, d2h = e2e_form(rhi, w, torch, args.steps, args.warmup,
-                                         codes[order[-1]], ljac[order[-1]], args.max_newton)
+            pc, guess = FORMS[order[-1]]
+            e2e_val, h2d, d2h = e2e_form(rhi, w, torch, args.steps, args.warmup, pc,
+                                         args.limiter_jacobian, args.max_newton, guess,
+                                         weights if guess == rhi.RHI_GUESS_LEARNED else None)
             line["e2e"] = {"value": world * e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                            "d2h_bytes_per_step": d2h}
         if not args.no_cpu_baseline:

@@ -72,6 +72,11 @@ typedef struct {
     double tau;             /* fraction-to-boundary of the positivity cap (0 < tau < 1)      */
     double lam_min;         /* smallest line-search parameter                                */
     double mlp_gate;        /* learned guess: predicted changes below this keep U^n          */
+    double mlp_ood;         /* learned guess: cells with a normalised feature |(x - mean) /
+                               scale| above this keep U^n (0: no such gate)                 */
+    int mlp_restart;        /* learned guess: Newton restarts from U^n when the learned start
+                               has not converged after this many iterations, or stagnates
+                               (||f|| above 0.9 of its value two iterations earlier); 0: never */
     double growth_max;      /* watchdog line search: a full step may raise ||f|| up to
                                growth_max times the best ||f|| of the step ...               */
     int watchdog;           /* ... for at most this many Newton iterations in a row          */
@@ -103,6 +108,7 @@ typedef struct {
     int lam_min_steps;      /* line searches that ended at lam_min                           */
     int guess_used;         /* RHI_GUESS_* actually used (learned falls back to previous)    */
     int launches;           /* kernel launches of the last step                              */
+    int guess_restarts;     /* 1 when Newton abandoned the learned start for U^n (mlp_restart) */
     double res_initial;     /* ||f(U_0)|| (eq. rmsnorm, scaled)                              */
     double res_final;       /* ||f(U^{n+1})||                                                */
     double res_guess_prev;  /* ||f(U^n)|| when a learned guess was tried, else 0             */
@@ -171,6 +177,13 @@ int rhi_get_stats(rhi_handle h, rhi_stats* out);
 int rhi_linearize(rhi_handle h, double dt, double a, double adot, double* f, double* S_diag,
                   double* S_lo, double* S_hi, double* rhs, int on_device);
 
+/* Scaled residual f(U) of eq. nonlinear_residual (with eq. scalings) of the step from the
+   current state over dt, at the given iterate U = (e_c, n_1 .. n_Ns, E), each N long
+   (e_c = e - e^n).  Writes f ((N_s + 2) x N, may be NULL) and its RMS norm (eq. rmsnorm, may
+   be NULL).  An inspection entry point: it uses the step's work buffers. */
+int rhi_residual(rhi_handle h, double dt, double a, double adot, const double* U, double* f,
+                 double* norm, int on_device);
+
 /* Applies the configured preconditioner (one V-cycle or Jacobi) of the Schur matrix built by
    the last rhi_linearize to r (N), writing z (N). */
 int rhi_precond_apply(rhi_handle h, const double* r, double* z, int on_device);
@@ -178,8 +191,12 @@ int rhi_precond_apply(rhi_handle h, const double* r, double* z, int on_device);
 /* Per-kernel device time: with profiling on, every launch is bracketed by CUDA events on the
    handle's stream and accumulated per kernel name.  rhi_kernel_times writes up to max
    entries (names as NUL-terminated strings of at most 47 chars in names[48*i..], total ms,
-   launch count) and returns the number of kernels (>= 0) or -RHI_ERR_*. */
+   launch count) and returns the number of kernels (>= 0) or -RHI_ERR_*.
+   rhi_set_profiling_names restricts the events to launches of the comma-separated kernel
+   names (NULL or "" times every launch), so that timing one kernel leaves the others
+   unbracketed. */
 int rhi_set_profiling(rhi_handle h, int on);
+int rhi_set_profiling_names(rhi_handle h, const char* names);
 int rhi_kernel_times(rhi_handle h, int max, char* names, double* total_ms, int* launches);
 
 /* Learned Newton initial guess (an addition; Sec. 3.2 leaves the initial iterate free): a
@@ -206,6 +223,11 @@ int rhi_mlp_features(rhi_handle h, double dt, double a, float* X, int on_device)
    rhi_set_state) to the current state. */
 int rhi_mlp_targets(rhi_handle h, const double* E_old, const double* e_old,
                     const double* n_old, float* Y, int on_device);
+/* The learned guess U_0 = (e_c, n_1 .. n_Ns, E) ((N_s + 2) x N) that rhi_implicit_step with
+   RHI_GUESS_LEARNED would start from (before its comparison with U^n): the network's outputs
+   decoded (E' = E 10^o0, e' = e 10^o1, x_HI' = 1 / (1 + exp(-o2)), He fractions by softmax of
+   o3..o5), cells whose predicted changes all stay below params.mlp_gate keeping U^n. */
+int rhi_mlp_guess(rhi_handle h, double dt, double a, double* U0, int on_device);
 /* Network outputs Y (n x 6) for features X (n x 9) on the tensor cores (BF16 weights). */
 int rhi_mlp_forward(rhi_handle h, const float* X, float* Y, long long n, int on_device);
 /* Mean squared error over the n samples and its gradient wrt the FP32 weights (FP32

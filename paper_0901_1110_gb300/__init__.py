@@ -33,7 +33,7 @@ class rhi_params(C.Structure):
                 ("m_grey", C.c_int), ("isothermal", C.c_int), ("limiter", C.c_int),
                 ("kappa_floor", C.c_double), ("u_e", C.c_double), ("u_n", C.c_double),
                 ("u_E", C.c_double), ("tau", C.c_double), ("lam_min", C.c_double),
-                ("mlp_gate", C.c_double), ("growth_max", C.c_double), ("watchdog", C.c_int), ("limiter_jacobian", C.c_int),
+                ("mlp_gate", C.c_double), ("mlp_ood", C.c_double), ("mlp_restart", C.c_int), ("growth_max", C.c_double), ("watchdog", C.c_int), ("limiter_jacobian", C.c_int),
                 ("max_newton", C.c_int), ("max_pcg", C.c_int), ("guess", C.c_int),
                 ("precond", C.c_int), ("mg_levels", C.c_int), ("mg_pre", C.c_int),
                 ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double),
@@ -44,7 +44,8 @@ class rhi_params(C.Structure):
 class rhi_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("newton_its", C.c_int), ("pcg_its", C.c_int),
                 ("vcycles", C.c_int), ("backtracks", C.c_int), ("lam_min_steps", C.c_int),
-                ("guess_used", C.c_int), ("launches", C.c_int), ("res_initial", C.c_double),
+                ("guess_used", C.c_int), ("launches", C.c_int), ("guess_restarts", C.c_int),
+                ("res_initial", C.c_double),
                 ("res_final", C.c_double), ("res_guess_prev", C.c_double), ("ms", C.c_double),
                 ("res_history", C.c_double * 64)]
 
@@ -65,7 +66,10 @@ _SIGS = {
     "rhi_linearize": (C.c_int, [_P, C.c_double, C.c_double, C.c_double, _P, _P, _P, _P, _P,
                                 C.c_int]),
     "rhi_precond_apply": (C.c_int, [_P, _P, _P, C.c_int]),
+    "rhi_residual": (C.c_int, [_P, C.c_double, C.c_double, C.c_double, _P, _P, _D, C.c_int]),
+    "rhi_mlp_guess": (C.c_int, [_P, C.c_double, C.c_double, _P, C.c_int]),
     "rhi_set_profiling": (C.c_int, [_P, C.c_int]),
+    "rhi_set_profiling_names": (C.c_int, [_P, C.c_char_p]),
     "rhi_kernel_times": (C.c_int, [_P, C.c_int, C.c_char_p, _D, C.POINTER(C.c_int)]),
     "rhi_rms_norm_noalloc": (C.c_int, [_P, C.c_longlong, C.c_longlong, _P, _P]),
     "rhi_mlp_set_weights": (C.c_int, [_P, _P, C.c_size_t]),
@@ -253,6 +257,15 @@ class Solver:
         return dict(f=f.reshape(nv, self.N), diag=d, face=lo.reshape(3, self.N),
                     face_hi=hi.reshape(3, self.N), rhs=r)
 
+    def residual(self, U, dt, a=1.0, adot=0.0):
+        """Scaled residual ((ns + 2) x N) and its RMS norm at iterate U = (e_c, n, E)."""
+        U = np.ascontiguousarray(U, dtype=np.float64).ravel()
+        f = np.empty_like(U)
+        nrm = C.c_double()
+        self._check(lib().rhi_residual(self.h, dt, a, adot, U.ctypes.data, f.ctypes.data,
+                                       C.byref(nrm), 0), "rhi_residual")
+        return f.reshape(self.ns + 2, self.N), nrm.value
+
     def precond_apply(self, r):
         r = np.ascontiguousarray(r, dtype=np.float64)
         z = np.empty_like(r)
@@ -288,6 +301,12 @@ class Solver:
             raise TypeError("all buffers on the host or all on the device")
         self._check(lib().rhi_mlp_targets(self.h, pE, pe, pn, pY, dev), "rhi_mlp_targets")
         return Y
+
+    def mlp_guess(self, dt, a=1.0):
+        """The decoded learned guess (e_c, n, E) as a ((ns + 2) x N) array."""
+        U = np.empty((self.ns + 2) * self.N)
+        self._check(lib().rhi_mlp_guess(self.h, dt, a, U.ctypes.data, 0), "rhi_mlp_guess")
+        return U.reshape(self.ns + 2, self.N)
 
     def mlp_forward(self, X, out=None):
         n = X.shape[0]
@@ -327,7 +346,10 @@ class Solver:
                     "rhi_mlp_train")
         return loss.value
 
-    def set_profiling(self, on):
+    def set_profiling(self, on, names=None):
+        """Per-launch CUDA events on (optionally only for the given kernel names) or off."""
+        self._check(lib().rhi_set_profiling_names(self.h, ",".join(names).encode() if names else None),
+                    "rhi_set_profiling_names")
         return self._check(lib().rhi_set_profiling(self.h, int(on)), "rhi_set_profiling")
 
     def kernel_times(self):

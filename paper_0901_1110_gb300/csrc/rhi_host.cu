@@ -36,9 +36,11 @@ struct Profiler : LaunchHook {
         cudaEventCreate(&e);
         return e;
     }
+    std::vector<std::string> only;     // when non-empty: time only launches of these names
     void begin(const char* name) override {
         ++launches;
         if (!on) return;
+        if (!only.empty() && std::find(only.begin(), only.end(), name) == only.end()) return;
         cur = name;
         cur_a = get();
         cudaEventRecord(cur_a, st);
@@ -516,7 +518,7 @@ int validate_params(const rhi_params* p) {
     if (!(p->growth_max >= 1.0) || p->watchdog < 0) return 0;
     if (p->max_newton < 0 || p->max_pcg < 1) return 0;
     if (p->guess < 0 || p->guess > RHI_GUESS_LEARNED) return 0;
-    if (!(p->mlp_gate >= 0.0)) return 0;
+    if (!(p->mlp_gate >= 0.0) || !(p->mlp_ood >= 0.0) || p->mlp_restart < 0) return 0;
     if (p->precond < 0 || p->precond > RHI_PRECOND_MG_FP32) return 0;
     if (p->mg_levels < 1 || p->mg_pre < 1 || p->mg_post < 0 || p->mg_coarse_sweeps < 1) return 0;
     if (p->limiter_jacobian != 0 && p->limiter_jacobian != 1) return 0;
@@ -556,6 +558,7 @@ MlpArgs mlp_args(const rhi_ctx* h, double dt, double a) {
     A.gam_per_E = C_LIGHT * h->prm.pgam[0] / (a * a * a);
     A.E = h->E_s; A.e = h->e_s; A.n = h->n_s; A.nH = h->nH; A.src = h->src;
     A.gate = (float)h->prm.mlp_gate;
+    A.ood = (float)h->prm.mlp_ood;
     A.isothermal = h->prm.isothermal;
     return A;
 }
@@ -611,6 +614,8 @@ int rhi_params_default(rhi_params* p, int n_species) {
     p->tau = 0.99;
     p->lam_min = 1.0 / 16.0;
     p->mlp_gate = 1e-3;
+    p->mlp_ood = 6.0;
+    p->mlp_restart = 12;
     p->growth_max = 1e3;
     p->watchdog = 3;
     p->limiter_jacobian = 0;
@@ -803,6 +808,22 @@ int rhi_set_profiling(rhi_handle h, int on) {
     return RHI_OK;
 }
 
+int rhi_set_profiling_names(rhi_handle h, const char* names) {
+    if (!h) return RHI_ERR_ARG;
+    h->prof.only.clear();
+    if (names) {
+        std::string s(names);
+        size_t a = 0;
+        while (a <= s.size()) {
+            size_t b = s.find(',', a);
+            if (b == std::string::npos) b = s.size();
+            if (b > a) h->prof.only.push_back(s.substr(a, b - a));
+            a = b + 1;
+        }
+    }
+    return RHI_OK;
+}
+
 int rhi_kernel_times(rhi_handle h, int max, char* names, double* total_ms, int* launches) {
     if (!h) return -RHI_ERR_ARG;
     h->prof.resolve();
@@ -864,6 +885,60 @@ int rhi_linearize(rhi_handle h, double dt, double a, double adot, double* f, dou
     CK(cudaStreamSynchronize(h->st));
     h->prof.resolve();
     h->have_linear = true;
+    return RHI_OK;
+}
+
+int rhi_residual(rhi_handle h, double dt, double a, double adot, const double* U, double* f,
+                 double* norm, int on_device) {
+    if (!h) return RHI_ERR_ARG;
+    if (!h->have_state) return fail(h, RHI_ERR_STATE, "rhi_residual: no state");
+    if (!U || !(dt > 0.0) || !(a > 0.0)) return fail(h, RHI_ERR_ARG, "rhi_residual: bad arguments");
+    h->have_linear = false;
+    const StepParams P = make_params(h, dt, a, adot);
+    const long long N = h->N;
+    const size_t bytes = (size_t)h->nv * N * sizeof(double);
+    int rc;
+    // g^n from the state, then f at the given iterate (work iterate 1, Schur set 1)
+    if ((rc = kappa(h, P, h->n_s, h->kap[0]))) return rc;
+    if ((rc = faces(h, P, h->E_s, h->kap[0], h->W[0], h->PQ[0]))) return rc;
+    PhysBuffers B = state_buffers(h);
+    B.W = h->W[0]; B.PQ = h->PQ[0]; B.diag_ns = h->diag_ns[0];
+    B.diag = h->diag[0]; B.rhs = h->rhs[0]; B.fMt = h->fMt[0]; B.MiU = h->MiU[0];
+    if ((rc = cell(h, P, MODE_PREP, B))) return rc;
+    CK(cudaMemcpyAsync(h->U[1], U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+    if ((rc = kappa(h, P, U_n(h, 1), h->kap[1]))) return rc;
+    if ((rc = faces(h, P, U_E(h, 1), h->kap[1], h->W[1], h->PQ[1]))) return rc;
+    PhysBuffers C = state_buffers(h);
+    C.ec = U_ec(h, 1); C.n = U_n(h, 1); C.E = U_E(h, 1); C.W = h->W[1];
+    C.PQ = h->PQ[1]; C.diag_ns = h->diag_ns[1];
+    C.diag = h->diag[1]; C.rhs = h->rhs[1]; C.fMt = h->fMt[1]; C.MiU = h->MiU[1];
+    if (f) C.f_out = on_device ? f : h->U[0];
+    if ((rc = cell(h, P, MODE_ITER, C))) return rc;
+    double r = 0.0;
+    if ((rc = residual_norm(h, ncell_blocks(h), &r))) return rc;
+    if (norm) *norm = r;
+    if (f && !on_device) CK(cudaMemcpyAsync(f, h->U[0], bytes, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->prof.resolve();
+    return RHI_OK;
+}
+
+int rhi_mlp_guess(rhi_handle h, double dt, double a, double* U0, int on_device) {
+    if (!h) return RHI_ERR_ARG;
+    if (!h->have_state) return fail(h, RHI_ERR_STATE, "rhi_mlp_guess: no state");
+    if (!h->mlp_ready) return fail(h, RHI_ERR_STATE, "rhi_mlp_guess: no weights set");
+    if (!U0 || !(dt > 0.0) || !(a > 0.0)) return fail(h, RHI_ERR_ARG, "rhi_mlp_guess: bad arguments");
+    MlpArgs A = mlp_args(h, dt, a);
+    A.U0 = on_device ? U0 : h->U[1];
+    {
+        Scope s(h->prof, "mlp_guess");
+        CK(launch_mlp_infer(A, h->mlp_pk, nullptr, nullptr, 0, 1, h->st));
+    }
+    if (!on_device)
+        CK(cudaMemcpyAsync(U0, h->U[1], (size_t)h->nv * h->N * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->have_linear = false;
+    h->prof.resolve();
     return RHI_OK;
 }
 
@@ -964,7 +1039,29 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
     double r_best = res;
     int bad = 0;
     S.res_history[0] = res;
+    int k_start = 0;         // iteration at which the current start was taken
     while (!(res < newton_tol) && k < h->prm.max_newton) {
+        const bool stalled = k - k_start >= 2 && k < RHI_MAX_HISTORY &&
+                             res > 0.9 * S.res_history[k - 2];
+        if (S.guess_used == RHI_GUESS_LEARNED && h->prm.mlp_restart > 0 &&
+            (k - k_start >= h->prm.mlp_restart || stalled)) {
+            // the learned start has not converged in mlp_restart iterations: restart from U^n
+            if ((rc = kappa(h, P, h->n_s, h->kap[0]))) return rc;
+            if ((rc = faces(h, P, h->E_s, h->kap[0], h->W[0], h->PQ[0]))) return rc;
+            PhysBuffers C = state_buffers(h);
+            C.W = h->W[0]; C.PQ = h->PQ[0]; C.diag_ns = h->diag_ns[0];
+            C.diag = h->diag[0]; C.rhs = h->rhs[0]; C.fMt = h->fMt[0]; C.MiU = h->MiU[0];
+            if ((rc = cell(h, P, MODE_PREP, C))) return rc;
+            if ((rc = residual_norm(h, ncell_blocks(h), &res))) return rc;
+            cur = -1;
+            set = 0;
+            r_best = res;
+            bad = 0;
+            k_start = k;
+            S.guess_used = RHI_GUESS_PREVIOUS;
+            S.guess_restarts = 1;
+            if (res < newton_tol) break;
+        }
         const double* Wk = h->W[cur < 0 ? 0 : cur];
         set_op0(h, P, set, Wk);
         if ((rc = precond_setup(h))) return rc;

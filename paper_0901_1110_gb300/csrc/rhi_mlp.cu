@@ -162,9 +162,13 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_mlp_infer(const MlpArgs A,
 #pragma unroll
             for (int q = 0; q < MLP_IN; ++q) f[q] = sw.mean[q];
         }
+        bool ood = false;
 #pragma unroll
-        for (int q = 0; q < 16; ++q)
-            xs[warp][lane][q] = __float2bfloat16_rn(q < MLP_IN ? (f[q] - sw.mean[q]) * sw.iscale[q] : 0.0f);
+        for (int q = 0; q < 16; ++q) {
+            const float xn = q < MLP_IN ? (f[q] - sw.mean[q]) * sw.iscale[q] : 0.0f;
+            ood |= A.ood > 0.0f && fabsf(xn) > A.ood;
+            xs[warp][lane][q] = __float2bfloat16_rn(xn);
+        }
         __syncwarp();
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
@@ -208,21 +212,24 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_mlp_infer(const MlpArgs A,
                 const double xHI = 1.0 / (1.0 + exp(-(double)o[2]));
                 double nHeI = 0.0, nHeII = 0.0;
                 if (A.ns == 3) {
+                    // softmax in FP64: n_HeI + n_HeII stays below n_He to rounding, so the
+                    // derived n_HeIII of the guess is not negative beyond the positivity cap's
+                    // tolerance (an FP32 softmax can overshoot by 1e-7 n_He and freeze the cell)
                     const double nHe = A.y_he * nH;
-                    const float mx = fmaxf(o[3], fmaxf(o[4], o[5]));
-                    const float z0 = __expf(o[3] - mx), z1 = __expf(o[4] - mx), z2 = __expf(o[5] - mx);
-                    const float iz = 1.0f / (z0 + z1 + z2);
+                    const double mx = fmax((double)o[3], fmax((double)o[4], (double)o[5]));
+                    const double z0 = exp(o[3] - mx), z1 = exp(o[4] - mx), z2 = exp(o[5] - mx);
+                    const double iz = 1.0 / (z0 + z1 + z2);
                     const double f0 = A.n[A.N + c] / nHe, f1 = A.n[2 * A.N + c] / nHe;
                     const double f2 = 1.0 - f0 - f1;
-                    change = fmaxf(change, fabsf(logf(fmaxf(z0 * iz, FLOOR_F)) - logf(fmaxf((float)f0, FLOOR_F))));
-                    change = fmaxf(change, fabsf(logf(fmaxf(z1 * iz, FLOOR_F)) - logf(fmaxf((float)f1, FLOOR_F))));
-                    change = fmaxf(change, fabsf(logf(fmaxf(z2 * iz, FLOOR_F)) - logf(fmaxf((float)f2, FLOOR_F))));
-                    nHeI = nHe * (double)(z0 * iz);
-                    nHeII = nHe * (double)(z1 * iz);
+                    change = fmaxf(change, fabsf((float)(log(fmax(z0 * iz, 1e-30)) - log(fmax(f0, 1e-30)))));
+                    change = fmaxf(change, fabsf((float)(log(fmax(z1 * iz, 1e-30)) - log(fmax(f1, 1e-30)))));
+                    change = fmaxf(change, fabsf((float)(log(fmax(z2 * iz, 1e-30)) - log(fmax(f2, 1e-30)))));
+                    nHeI = nHe * (z0 * iz);
+                    nHeII = nHe * (z1 * iz);
                 }
                 const long long N = A.N;
                 double* U = A.U0;
-                if (change < A.gate) {
+                if (change < A.gate || ood) {
                     U[c] = 0.0;
                     for (int s = 0; s < A.ns; ++s) U[(1 + s) * N + c] = A.n[s * N + c];
                     U[(1 + A.ns) * N + c] = E0;

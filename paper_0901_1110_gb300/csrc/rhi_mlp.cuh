@@ -36,6 +36,7 @@ struct MlpArgs {
     const double* nH;
     const double* src;
     float gate;
+    float ood;                                // |normalised feature| above this keeps U^n
     int isothermal;                           // guess keeps e_c = 0
     double* U0;                               // guess (e_c | n | E), MODE 1
 };
