@@ -21,7 +21,9 @@ Readings of the paper made here (each also listed in the design notes):
   D = c / (3 max(kappa, kappa_floor)).
 * The Newton matrix either lags D entirely (``limiter_jacobian = "lagged"``: the Schur matrix is
   symmetric, as CG needs) or, as Sec. 3.2.1 states, keeps dD/dE and lags only the opacity
-  (``"E"``: a non-symmetric Schur matrix).
+  (``"E"``: a non-symmetric Schur matrix), or keeps both dD/dE and the opacity's species
+  dependence (``"exact"``: the true Jacobian of f; its Schur complement is still a 7-point
+  operator in E because the cell-local blocks are eliminated cell by cell).
 """
 from dataclasses import dataclass, field
 
@@ -57,7 +59,8 @@ class Problem:
     u_E: float = 1.0
     tau: float = 0.99                  # fraction-to-boundary of the positivity limiter
     lam_min: float = 1.0 / 16.0         # smallest line-search parameter
-    limiter_jacobian: str = "lagged"   # "lagged": D frozen in J; "E": dD/dE kept, kappa lagged
+    limiter_jacobian: str = "lagged"   # "lagged": D frozen in J; "E": dD/dE kept, kappa lagged;
+                                       # "exact": dD/dE and dD/dkappa dkappa/dn kept
     growth_max: float = 1e3            # watchdog: a full step may raise ||f|| up to this factor
     watchdog: int = 3                  # ... for at most this many steps without a new best ||f||
     rates: object = field(default=None)
@@ -276,6 +279,42 @@ def face_coefficient_derivatives(p, Ea, Eb, ka, kb, a):
     return W, f * dRa, f * dRb
 
 
+def face_coefficient_kappa_derivative(p, Ea, Eb, ka, kb, a):
+    """dW/dkappa_face of ``face_coefficient`` at fixed E: with the limiter
+    dD/dkappa = -c (12 kappa^2 + 12 kappa R + R^2) / (6 kappa^2 + 3 kappa R + R^2)^2 (the
+    quotient rule on eq. limiter), without it -c / (3 kappa^2) above the floor, else 0.  Each
+    cell's kappa enters the face mean with weight 1/2."""
+    kap = 0.5 * (ka + kb)
+    c = cl.C_LIGHT
+    if p.limiter:
+        Ebar = 0.5 * (Ea + Eb)
+        R_min = 1.0 / (a * max(p.nx, p.ny, p.nz) * p.dx)
+        R = np.maximum(np.abs(Eb - Ea) / (a * p.dx * Ebar), R_min)
+        den = 6.0 * kap ** 2 + 3.0 * kap * R + R ** 2
+        dD = -c * (12.0 * kap ** 2 + 12.0 * kap * R + R ** 2) / den ** 2
+    else:
+        dD = np.where(kap > p.kappa_floor, -c / (3.0 * np.maximum(kap, p.kappa_floor) ** 2), 0.0)
+    return dD / (a * a * p.dx * p.dx)
+
+
+def diffusion_kappa_block(p, E, kap, a, dth, nbt):
+    """d(dt theta * diffusion term of cell i) / d kappa_j for j = i (diag) and the flux-carrying
+    neighbours (rows, cols, vals): face f between i and nb contributes
+    dt theta (1/2) dW_f/dkappa_f (E_i - E_nb) to both."""
+    nb, valid = nbt
+    N = p.N
+    cells = np.arange(N)
+    diag = np.zeros(N)
+    rows, cols, vals = [], [], []
+    for d in range(6):
+        m = valid[d]
+        Enb, knb = E[nb[d]], kap[nb[d]]
+        v = dth * 0.5 * face_coefficient_kappa_derivative(p, E, Enb, kap, knb, a) * (E - Enb)
+        diag += np.where(m, v, 0.0)
+        rows.append(cells[m]); cols.append(nb[d][m]); vals.append(v[m])
+    return diag, rows, cols, vals
+
+
 def face_weights(p, E, kap, a, nbt=None):
     """W[d, cell] for the six faces of every cell (0 on zero-flux boundary faces)."""
     nb, valid = neighbor_table(p) if nbt is None else nbt
@@ -386,7 +425,7 @@ def diffusion_block(p, E, kap, a, dth, nbt):
     for d in range(6):
         m = valid[d]
         Enb, knb = E[nb[d]], kap[nb[d]]
-        if p.limiter_jacobian == "E":
+        if p.limiter_jacobian in ("E", "exact"):
             W, dWi, dWn = face_coefficient_derivatives(p, E, Enb, kap, knb, a)
             dE = E - Enb
             di = W + dWi * dE
@@ -401,7 +440,9 @@ def diffusion_block(p, E, kap, a, dth, nbt):
 
 def full_jacobian(p, U, eh, dt, a, adot, T_fixed=None, nbt=None):
     """The whole scaled Newton matrix (unreduced), sparse, variable-major ordering:
-    rows/cols [v * N + cell] for v in (e_c, n_1.., E).  D is lagged (frozen at U)."""
+    rows/cols [v * N + cell] for v in (e_c, n_1.., E).  D is lagged (frozen at U), keeps
+    dD/dE ("E"), or keeps dD/dE and the opacity's species dependence ("exact"), which adds
+    E-row entries in the species columns of the cell and of its neighbours."""
     ns, nm, N = p.ns, p.ns + 1, p.N
     M, Ucol, Lrow, Dloc, lt = local_blocks(p, U, eh, dt, a, adot, T_fixed)
     nbt = neighbor_table(p) if nbt is None else nbt
@@ -414,6 +455,16 @@ def full_jacobian(p, U, eh, dt, a, adot, T_fixed=None, nbt=None):
         rows.append(r * N + cells); cols.append(nm * N + cells); vals.append(Ucol[:, r])
         rows.append(nm * N + cells); cols.append(r * N + cells); vals.append(Lrow[:, r])
     rows.append(nm * N + cells); cols.append(nm * N + cells); vals.append(Dloc + ddiag)
+    if p.limiter_jacobian == "exact":
+        kdiag, krows, kcols, kvals = diffusion_kappa_block(p, U[1 + ns], lt["kappa"], a,
+                                                           dt * p.theta, nbt)
+        sk = p.grey["sk"]
+        for X in range(ns):
+            # d kappa / d n_X = sk_X / a^3; scaled entry d(f_E/u_E) / d(n_X/u_n)
+            fac = sk[X] / a ** 3 * p.u_n / p.u_E
+            rows.append(nm * N + cells); cols.append((1 + X) * N + cells); vals.append(fac * kdiag)
+            for rr, cc, vv in zip(krows, kcols, kvals):
+                rows.append(nm * N + rr); cols.append((1 + X) * N + cc); vals.append(fac * vv)
     for rr, cc, vv in zip(drows, dcols, dvals):
         rows.append(nm * N + rr); cols.append(nm * N + cc); vals.append(vv)
     J = sparse.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),

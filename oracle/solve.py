@@ -147,6 +147,8 @@ def schur_system(p, U, f, eh, dt, a, adot, T_fixed=None, nbt=None):
     ns, nm, N = p.ns, p.ns + 1, p.N
     nbt = md.neighbor_table(p) if nbt is None else nbt
     nb, valid = nbt
+    if p.limiter_jacobian == "exact":
+        return _schur_from_full_jacobian(p, U, f, eh, dt, a, adot, T_fixed, nbt)
     M, Ucol, Lrow, Dloc, lt = md.local_blocks(p, U, eh, dt, a, adot, T_fixed)
     fs = f / p.scales()[:, None]
     fM = fs[:nm].T                                           # (N, nm)
@@ -162,6 +164,38 @@ def schur_system(p, U, f, eh, dt, a, adot, T_fixed=None, nbt=None):
     vals = [dS + ddiag] + dvals
     S = sparse.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                           shape=(N, N)).tocsr()
+    return S, rhs, fM_t, MiU
+
+
+def _schur_from_full_jacobian(p, U, f, eh, dt, a, adot, T_fixed, nbt):
+    """The Schur complement by sparse block algebra on the whole Newton matrix J: with the
+    local unknowns m = (e_c, n) and J_mm block diagonal (one (Ns+1)^2 block per cell),
+    S = J_EE - J_Em J_mm^-1 J_mE and rhs = J_Em J_mm^-1 f_m - f_E."""
+    nm, N = p.ns + 1, p.N
+    J = md.full_jacobian(p, U, eh, dt, a, adot, T_fixed, nbt).tocsr()
+    m_idx = np.arange(nm * N)
+    E_idx = np.arange(nm * N, (nm + 1) * N)
+    # per-cell blocks of J_mm (variable-major ordering: entry (r, s) of cell c at r N + c, s N + c)
+    Jc = J.tocoo()
+    M = np.zeros((N, nm, nm))
+    sel = (Jc.row < nm * N) & (Jc.col < nm * N)
+    r, s = Jc.row[sel], Jc.col[sel]
+    assert np.all(r % N == s % N), "J_mm is not block diagonal"
+    np.add.at(M, (r % N, r // N, s // N), Jc.data[sel])
+    JmE = J[m_idx][:, E_idx].tocoo()
+    Ucol = np.zeros((N, nm))
+    assert np.all(JmE.row % N == JmE.col), "J_mE is not cell-local"
+    np.add.at(Ucol, (JmE.col, JmE.row // N), JmE.data)
+    fs = f / p.scales()[:, None]
+    fM_t = np.linalg.solve(M, fs[:nm].T[:, :, None])[:, :, 0]
+    MiU = np.linalg.solve(M, Ucol[:, :, None])[:, :, 0]
+    cells = np.arange(N)
+    MiU_mat = sparse.coo_matrix((MiU.T.ravel(), (np.repeat(np.arange(nm), N) * N + np.tile(cells, nm),
+                                                 np.tile(cells, nm))), shape=(nm * N, N)).tocsr()
+    JEm = J[E_idx][:, m_idx]
+    JEE = J[E_idx][:, E_idx]
+    S = (JEE - JEm @ MiU_mat).tocsr()
+    rhs = JEm @ fM_t.T.ravel() - fs[nm]
     return S, rhs, fM_t, MiU
 
 
