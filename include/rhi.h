@@ -82,7 +82,9 @@ typedef struct {
     int watchdog;           /* ... for at most this many Newton iterations in a row          */
     int limiter_jacobian;   /* 0: D lagged in the Newton matrix (symmetric S, CG);
                                1: dD/dE kept and only the opacity lagged, as Sec. 3.2.1
-                               states (non-symmetric S, BiCGStab with the same V-cycle)     */
+                               states (non-symmetric S, BiCGStab with the same V-cycle);
+                               2: exact, dD/dE and D's opacity dependence on the species
+                               kept (non-symmetric 7-point S, BiCGStab)                     */
     int max_newton;         /* Newton iterations per step                                    */
     int max_pcg;            /* CG iterations per Newton iteration                            */
     int guess;              /* RHI_GUESS_*                                                   */

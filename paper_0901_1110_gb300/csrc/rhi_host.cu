@@ -107,6 +107,7 @@ struct rhi_ctx {
     double* kap[2] = {nullptr, nullptr};
     double* W[2] = {nullptr, nullptr};
     double* PQ[2] = {nullptr, nullptr};         // Newton-matrix face entries (dD/dE kept)
+    double* Kf[2] = {nullptr, nullptr};         // exact matrix: (1/2) dW/dkappa dE per face
     double* diag_ns[2] = {nullptr, nullptr};
     double* g = nullptr;
     double *diag[2] = {nullptr, nullptr}, *rhs[2] = {nullptr, nullptr};
@@ -470,10 +471,17 @@ int cell(rhi_ctx* h, const StepParams& P, int mode, PhysBuffers B) {
 }
 int ncell_blocks(const rhi_ctx* h) { return (int)((h->N + cell_block_size() - 1) / cell_block_size()); }
 
-int faces(rhi_ctx* h, const StepParams& P, const double* E, const double* kap, double* W,
-          double* PQ) {
+int faces(rhi_ctx* h, const StepParams& P, const double* E, const double* kap, int b) {
     Scope s(h->prof, "faces_limiter");
-    CK(launch_faces(P, E, kap, W, PQ, h->st));
+    CK(launch_faces(P, E, kap, h->W[b], h->PQ[b], h->Kf[b], h->st));
+    return RHI_OK;
+}
+// exact Newton matrix: fold the opacity coupling into Schur set `set` built from buffer b
+int schur_kappa(rhi_ctx* h, const StepParams& P, int b, int set) {
+    if (h->prm.limiter_jacobian != 2) return RHI_OK;
+    Scope s(h->prof, "schur_kappa");
+    CK(launch_schur_kappa(P, h->ns, h->Kf[b], h->fMt[set], h->MiU[set], h->PQ[b], h->diag_ns[set],
+                          h->rhs[set], h->st));
     return RHI_OK;
 }
 int kappa(rhi_ctx* h, const StepParams& P, const double* n, double* kap) {
@@ -521,7 +529,7 @@ int validate_params(const rhi_params* p) {
     if (!(p->mlp_gate >= 0.0) || !(p->mlp_ood >= 0.0) || p->mlp_restart < 0) return 0;
     if (p->precond < 0 || p->precond > RHI_PRECOND_MG_FP32) return 0;
     if (p->mg_levels < 1 || p->mg_pre < 1 || p->mg_post < 0 || p->mg_coarse_sweeps < 1) return 0;
-    if (p->limiter_jacobian != 0 && p->limiter_jacobian != 1) return 0;
+    if (p->limiter_jacobian < 0 || p->limiter_jacobian > 2) return 0;
     if (!(p->mg_omega > 0.0 && p->mg_omega <= 1.0)) return 0;
     return 1;
 }
@@ -668,6 +676,7 @@ int rhi_create(const rhi_grid* grid, const rhi_bc* bc, const rhi_params* params,
         A(&h->diag[b], N); A(&h->rhs[b], N); A(&h->fMt[b], (size_t)h->nm * N);
         A(&h->MiU[b], (size_t)h->nm * N);
         if (params->limiter_jacobian) { A(&h->PQ[b], 6 * (size_t)N); A(&h->diag_ns[b], N); }
+        if (params->limiter_jacobian == 2) A(&h->Kf[b], 3 * (size_t)N);
     }
     if (params->limiter_jacobian) {
         A(&h->rh, N); A(&h->v, N); A(&h->s, N); A(&h->t, N); A(&h->ph, N); A(&h->sh, N);
@@ -850,7 +859,7 @@ int rhi_linearize(rhi_handle h, double dt, double a, double adot, double* f, dou
     const StepParams P = make_params(h, dt, a, adot);
     int rc;
     if ((rc = kappa(h, P, h->n_s, h->kap[0]))) return rc;
-    if ((rc = faces(h, P, h->E_s, h->kap[0], h->W[0], h->PQ[0]))) return rc;
+    if ((rc = faces(h, P, h->E_s, h->kap[0], 0))) return rc;
     PhysBuffers B = state_buffers(h);
     B.W = h->W[0];
     B.PQ = h->PQ[0]; B.diag_ns = h->diag_ns[0];
@@ -858,6 +867,7 @@ int rhi_linearize(rhi_handle h, double dt, double a, double adot, double* f, dou
     // the residual goes straight to a device destination, or via a free work buffer
     if (f) B.f_out = on_device ? f : h->U[1];
     if ((rc = cell(h, P, MODE_PREP, B))) return rc;
+    if ((rc = schur_kappa(h, P, 0, 0))) return rc;
     set_op0(h, P, 0, h->W[0]);
     if (h->prm.limiter_jacobian) set_opns(h, P, 0, h->PQ[0]);
     if ((rc = precond_setup(h))) return rc;
@@ -900,14 +910,14 @@ int rhi_residual(rhi_handle h, double dt, double a, double adot, const double* U
     int rc;
     // g^n from the state, then f at the given iterate (work iterate 1, Schur set 1)
     if ((rc = kappa(h, P, h->n_s, h->kap[0]))) return rc;
-    if ((rc = faces(h, P, h->E_s, h->kap[0], h->W[0], h->PQ[0]))) return rc;
+    if ((rc = faces(h, P, h->E_s, h->kap[0], 0))) return rc;
     PhysBuffers B = state_buffers(h);
     B.W = h->W[0]; B.PQ = h->PQ[0]; B.diag_ns = h->diag_ns[0];
     B.diag = h->diag[0]; B.rhs = h->rhs[0]; B.fMt = h->fMt[0]; B.MiU = h->MiU[0];
     if ((rc = cell(h, P, MODE_PREP, B))) return rc;
     CK(cudaMemcpyAsync(h->U[1], U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
     if ((rc = kappa(h, P, U_n(h, 1), h->kap[1]))) return rc;
-    if ((rc = faces(h, P, U_E(h, 1), h->kap[1], h->W[1], h->PQ[1]))) return rc;
+    if ((rc = faces(h, P, U_E(h, 1), h->kap[1], 1))) return rc;
     PhysBuffers C = state_buffers(h);
     C.ec = U_ec(h, 1); C.n = U_n(h, 1); C.E = U_E(h, 1); C.W = h->W[1];
     C.PQ = h->PQ[1]; C.diag_ns = h->diag_ns[1];
@@ -979,7 +989,7 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
 
     // ---- g^n and the initial iterate U_0
     if ((rc = kappa(h, P, h->n_s, h->kap[0]))) return rc;
-    if ((rc = faces(h, P, h->E_s, h->kap[0], h->W[0], h->PQ[0]))) return rc;
+    if ((rc = faces(h, P, h->E_s, h->kap[0], 0))) return rc;
     PhysBuffers B = state_buffers(h);
     B.W = h->W[0];
     B.PQ = h->PQ[0]; B.diag_ns = h->diag_ns[0];
@@ -1001,7 +1011,7 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
                 CK(launch_mlp_infer(A, h->mlp_pk, nullptr, nullptr, 0, 1, h->st));
             }
             if ((rc = kappa(h, P, U_n(h, 1), h->kap[1]))) return rc;
-            if ((rc = faces(h, P, U_E(h, 1), h->kap[1], h->W[1], h->PQ[1]))) return rc;
+            if ((rc = faces(h, P, U_E(h, 1), h->kap[1], 1))) return rc;
             PhysBuffers C = state_buffers(h);
             C.ec = U_ec(h, 1); C.n = U_n(h, 1); C.E = U_E(h, 1); C.W = h->W[1];
             C.PQ = h->PQ[1]; C.diag_ns = h->diag_ns[1];
@@ -1023,7 +1033,7 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
         if ((rc = cell(h, P, MODE_PREP_PREDICT, B))) return rc;
         cur = 0;
         if ((rc = kappa(h, P, U_n(h, 0), h->kap[0]))) return rc;
-        if ((rc = faces(h, P, U_E(h, 0), h->kap[0], h->W[0], h->PQ[0]))) return rc;
+        if ((rc = faces(h, P, U_E(h, 0), h->kap[0], 0))) return rc;
         PhysBuffers C = state_buffers(h);
         C.ec = U_ec(h, 0); C.n = U_n(h, 0); C.E = U_E(h, 0); C.W = h->W[0];
         C.PQ = h->PQ[0]; C.diag_ns = h->diag_ns[0];
@@ -1047,7 +1057,7 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
             (k - k_start >= h->prm.mlp_restart || stalled)) {
             // the learned start has not converged in mlp_restart iterations: restart from U^n
             if ((rc = kappa(h, P, h->n_s, h->kap[0]))) return rc;
-            if ((rc = faces(h, P, h->E_s, h->kap[0], h->W[0], h->PQ[0]))) return rc;
+            if ((rc = faces(h, P, h->E_s, h->kap[0], 0))) return rc;
             PhysBuffers C = state_buffers(h);
             C.W = h->W[0]; C.PQ = h->PQ[0]; C.diag_ns = h->diag_ns[0];
             C.diag = h->diag[0]; C.rhs = h->rhs[0]; C.fMt = h->fMt[0]; C.MiU = h->MiU[0];
@@ -1063,6 +1073,7 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
             if (res < newton_tol) break;
         }
         const double* Wk = h->W[cur < 0 ? 0 : cur];
+        if ((rc = schur_kappa(h, P, cur < 0 ? 0 : cur, set))) return rc;
         set_op0(h, P, set, Wk);
         if ((rc = precond_setup(h))) return rc;
         int its = 0;
@@ -1086,7 +1097,7 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
                                  h->MiU[set], U_ec(h, t), U_n(h, t), U_E(h, t), h->kap[t], h->st));
             }
             int r2;
-            if ((r2 = faces(h, P, U_E(h, t), h->kap[t], h->W[t], h->PQ[t]))) return r2;
+            if ((r2 = faces(h, P, U_E(h, t), h->kap[t], t))) return r2;
             PhysBuffers C = state_buffers(h);
             C.ec = U_ec(h, t); C.n = U_n(h, t); C.E = U_E(h, t); C.W = h->W[t];
             C.PQ = h->PQ[t]; C.diag_ns = h->diag_ns[1 - set];

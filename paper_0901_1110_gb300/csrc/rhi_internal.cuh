@@ -148,7 +148,10 @@ enum CellMode { MODE_PREP = 0, MODE_ITER = 1, MODE_PREP_PREDICT = 2 };
 cudaError_t launch_kappa(const StepParams& P, int ns, const double* n, double* kap,
                          cudaStream_t st);
 cudaError_t launch_faces(const StepParams& P, const double* E, const double* kap, double* W,
-                         double* PQ, cudaStream_t st);
+                         double* PQ, double* K, cudaStream_t st);
+cudaError_t launch_schur_kappa(const StepParams& P, int ns, const double* K, const double* fMt,
+                               const double* MiU, double* PQ, double* diag_ns, double* rhs,
+                               cudaStream_t st);
 cudaError_t launch_export_faces(const StepParams& P, const double* W, const double* PQ,
                                 double* S_lo, double* S_hi, cudaStream_t st);
 cudaError_t launch_cell(const StepParams& P, int ns, int mode, const PhysBuffers& B,

@@ -17,7 +17,6 @@ namespace rhi {
 
 namespace {
 
-constexpr float FLOOR_F = 1e-30f;
 constexpr int INF_WARPS = 4;                  // warps per inference block
 constexpr int TRAIN_BLOCK = 128;
 
@@ -25,22 +24,24 @@ constexpr int TRAIN_BLOCK = 128;
 // features of one cell (FP32 from the FP64 state)
 
 __device__ __forceinline__ void cell_features(const MlpArgs& A, long long c, float (&f)[MLP_IN]) {
+    // logarithms in FP64 (once per cell and step): the source ratio 4 pi eta dt / E and the
+    // field can leave the FP32 range in cells the radiation has not reached yet
     const double E = A.E[c], e = A.e[c], nH = A.nH[c];
     const double nHe = A.y_he * nH;
-    f[0] = log10f((float)(E * A.iu_E));
-    f[1] = log10f((float)(e * A.iu_e));
-    f[2] = log10f(fmaxf((float)(A.n[c] / nH), FLOOR_F));
+    f[0] = (float)log10(E * A.iu_E);
+    f[1] = (float)log10(e * A.iu_e);
+    f[2] = (float)log10(fmax(A.n[c] / nH, 1e-30));
     if (A.ns == 3) {
-        f[3] = log10f(fmaxf((float)(A.n[A.N + c] / nHe), FLOOR_F));
-        f[4] = log10f(fmaxf((float)(A.n[2 * A.N + c] / nHe), FLOOR_F));
+        f[3] = (float)log10(fmax(A.n[A.N + c] / nHe, 1e-30));
+        f[4] = (float)log10(fmax(A.n[2 * A.N + c] / nHe, 1e-30));
     } else {
         f[3] = 0.0f;
         f[4] = 0.0f;
     }
-    f[5] = log10f((float)(nH * A.iu_n));
-    f[6] = log10f((float)(A.dt * A.gam_per_E * E) + FLOOR_F);
-    f[7] = log10f(1.0f + (float)(A.src[c] * A.dt / E));
-    f[8] = log10f((float)(A.dt * 1e-12));
+    f[5] = (float)log10(nH * A.iu_n);
+    f[6] = (float)log10(A.dt * A.gam_per_E * E + 1e-30);
+    f[7] = (float)log10(1.0 + A.src[c] * A.dt / E);
+    f[8] = (float)log10(A.dt * 1e-12);
 }
 
 __global__ void k_mlp_features(const MlpArgs A, float* __restrict__ X) {

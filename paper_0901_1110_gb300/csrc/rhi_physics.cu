@@ -46,13 +46,21 @@ cudaError_t launch_kappa(const StepParams& P, int ns, const double* n, double* k
 // and t = dE / (E_a + E_b): P = W + R dD/dR (1 - t) / (a dx)^2, Q = W + R dD/dR (1 + t) / (a dx)^2
 // (both = W where R sits at its floor).
 
-struct FaceCoef { double W, P, Q; };
+//
+// The exact Newton matrix also keeps D's opacity dependence: K = (1/2) (dW/dkappa) dE per face,
+// with dD/dkappa = -c s^2 (12 kappa^2 s^2 + 12 kappa s q + q^2) / den^2 (the quotient rule on
+// eq. limiter; each cell's kappa enters the face mean with weight 1/2).
 
-template <bool PQ>
+struct FaceCoef { double W, P, Q, K; };
+
+// JM: 0 W only; 1 W, P, Q (dD/dE kept); 2 W, P, Q, K (exact)
+template <int JM>
 __device__ __forceinline__ FaceCoef face_coef(const StepParams& P, double Ea, double Eb,
                                               double ka, double kb) {
+    constexpr bool PQ = JM >= 1;
     const double kap = 0.5 * (ka + kb);
     FaceCoef r;
+    r.K = 0.0;
     if (P.limiter) {
         const double Esum = Ea + Eb;
         const double s = 0.5 * Esum / P.inv_adx;               // a dx Ebar
@@ -69,6 +77,9 @@ __device__ __forceinline__ FaceCoef face_coef(const StepParams& P, double Ea, do
         }
         const double iden = 1.0 / den;
         r.W = num * iden * P.inv_a2dx2;
+        if (JM == 2)
+            r.K = -0.5 * C_LIGHT * s * s * (12.0 * ks * ks + 12.0 * ks * q + q * q) * iden * iden *
+                  P.inv_a2dx2 * dE;
         if (qraw > P.R_min * s) {
             const double RdD = -C_LIGHT * q * q * (4.0 * ks + q) * s * iden * iden * P.inv_a2dx2;
             const double t = dE / Esum;
@@ -81,13 +92,16 @@ __device__ __forceinline__ FaceCoef face_coef(const StepParams& P, double Ea, do
     }
     r.W = C_LIGHT / (3.0 * fmax(kap, P.kappa_floor)) * P.inv_a2dx2;
     r.P = r.Q = r.W;
+    if (JM == 2 && kap > P.kappa_floor) r.K = -0.5 * r.W / kap * (Eb - Ea);
     return r;
 }
 
-template <bool PQ>
+template <int JM>
 __global__ void __launch_bounds__(256) k_faces(const StepParams P, const double* __restrict__ E,
                                                const double* __restrict__ kap,
-                                               double* __restrict__ W, double* __restrict__ PQv) {
+                                               double* __restrict__ W, double* __restrict__ PQv,
+                                               double* __restrict__ Kv) {
+    constexpr bool PQ = JM >= 1;
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= P.N) return;
     int i, j, k;
@@ -96,22 +110,92 @@ __global__ void __launch_bounds__(256) k_faces(const StepParams P, const double*
     const double Ec = E[c], kc = kap[c];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-        FaceCoef f{0.0, 0.0, 0.0};
-        if (b.has_lo[ax]) f = face_coef<PQ>(P, E[b.lo[ax]], Ec, kap[b.lo[ax]], kc);
+        FaceCoef f{0.0, 0.0, 0.0, 0.0};
+        if (b.has_lo[ax]) f = face_coef<JM>(P, E[b.lo[ax]], Ec, kap[b.lo[ax]], kc);
         W[ax * P.N + c] = f.W;
         if (PQ) {
             PQv[ax * P.N + c] = f.P;
             PQv[(3 + ax) * P.N + c] = f.Q;
         }
+        if (JM == 2) Kv[ax * P.N + c] = f.K;
     }
 }
 
 cudaError_t launch_faces(const StepParams& P, const double* E, const double* kap, double* W,
-                         double* PQ, cudaStream_t st) {
+                         double* PQ, double* K, cudaStream_t st) {
     const int b = 256;
     const unsigned g = (unsigned)((P.N + b - 1) / b);
-    if (PQ) k_faces<true><<<g, b, 0, st>>>(P, E, kap, W, PQ);
-    else k_faces<false><<<g, b, 0, st>>>(P, E, kap, W, nullptr);
+    if (PQ && K) k_faces<2><<<g, b, 0, st>>>(P, E, kap, W, PQ, K);
+    else if (PQ) k_faces<1><<<g, b, 0, st>>>(P, E, kap, W, PQ, nullptr);
+    else k_faces<0><<<g, b, 0, st>>>(P, E, kap, W, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+// Exact Newton matrix: the E row of a cell couples to the species of the cell and of its
+// face neighbours through D's opacity.  After the cell-local elimination
+// dn_j = -M_j^-1 f_M,j - M_j^-1 U_j dE_j, face f (lower cell l, upper cell u, stored at u) adds,
+// with rho_j = sum_X (dkappa/dn_X) (M^-1 U)_j,X and phi_j likewise with M^-1 f_M (scaled),
+//   P_f -= K_f rho_u,  Q_f += K_f rho_l,
+//   diag_u -= dt theta K_f rho_u,  diag_l += dt theta K_f rho_l,
+//   rhs_u += dt theta K_f (phi_l + phi_u),  rhs_l -= dt theta K_f (phi_l + phi_u).
+// Each thread owns its cell's three lower faces, so every write has one writer.
+template <int NS>
+__global__ void __launch_bounds__(256) k_schur_kappa(const StepParams P,
+                                                     const double* __restrict__ K,
+                                                     const double* __restrict__ fMt,
+                                                     const double* __restrict__ MiU,
+                                                     double* __restrict__ PQ,
+                                                     double* __restrict__ diag_ns,
+                                                     double* __restrict__ rhs) {
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long N = P.N;
+    if (c >= N) return;
+    int i, j, k;
+    cell_coords(P, c, i, j, k);
+    const Nbr b = neighbours(P, c, i, j, k);
+    const double kfac = P.u_n * P.iu_E * P.ia3;     // d kappa / d n_X = sk_X / a^3, scaled
+    auto rho = [&](long long q) {
+        double s = 0.0;
+#pragma unroll
+        for (int X = 0; X < NS; ++X) s += P.sk[X] * MiU[(1 + X) * N + q];
+        return kfac * s;
+    };
+    auto phi = [&](long long q) {
+        double s = 0.0;
+#pragma unroll
+        for (int X = 0; X < NS; ++X) s += P.sk[X] * fMt[(1 + X) * N + q];
+        return kfac * s;
+    };
+    const double rc = rho(c), pc = phi(c);
+    double dd = 0.0, dr = 0.0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        if (b.has_lo[ax]) {
+            const long long l = b.lo[ax];
+            const double Kf = K[ax * N + c];
+            PQ[ax * N + c] -= Kf * rc;
+            PQ[(3 + ax) * N + c] += Kf * rho(l);
+            dd -= Kf * rc;
+            dr += Kf * (phi(l) + pc);
+        }
+        if (b.has_hi[ax]) {
+            const long long h = b.hi[ax];
+            const double Kh = K[ax * N + h];
+            dd += Kh * rc;
+            dr -= Kh * (pc + phi(h));
+        }
+    }
+    diag_ns[c] += P.dth * dd;
+    rhs[c] += P.dth * dr;
+}
+
+cudaError_t launch_schur_kappa(const StepParams& P, int ns, const double* K, const double* fMt,
+                               const double* MiU, double* PQ, double* diag_ns, double* rhs,
+                               cudaStream_t st) {
+    const int b = 256;
+    const unsigned g = (unsigned)((P.N + b - 1) / b);
+    if (ns == 1) k_schur_kappa<1><<<g, b, 0, st>>>(P, K, fMt, MiU, PQ, diag_ns, rhs);
+    else k_schur_kappa<3><<<g, b, 0, st>>>(P, K, fMt, MiU, PQ, diag_ns, rhs);
     return cudaGetLastError();
 }
 

@@ -66,16 +66,20 @@ def test_grey_constants_match_oracle_quadrature(rhi):
         assert abs(a["eps"] / b["eps"] - 1) < 1e-12
 
 
-@pytest.mark.parametrize("ljac", [0, 1])
+LJAC = {0: "lagged", 1: "E", 2: "exact"}
+
+
+@pytest.mark.parametrize("ljac", [0, 1, 2])
 @pytest.mark.parametrize("name", list(WL))
 def test_linear_system_matches_oracle(rhi, name, ljac):
     """Residual f(U^n) (eq. nonlinear_residual), Schur matrix S = D - L M^-1 U and right-hand
     side L M^-1 f_M - f_E (Sec. 3.2.1) of the first Newton system, cell by cell, with D lagged
-    (symmetric S) and with dD/dE kept (non-symmetric S)."""
+    (symmetric S), with dD/dE kept, and exact (dD/dE and D's opacity dependence kept: the E
+    rows reach the neighbours' species, folded into S by the cell-local elimination)."""
     w = WL[name]
     s = rhi.solver_for_workload(w, limiter_jacobian=ljac)
     lin = s.linearize(w.dt)
-    p = oracle_problem(w, limiter_jacobian="E" if ljac else "lagged")
+    p = oracle_problem(w, limiter_jacobian=LJAC[ljac])
     st = w.state()
     U = md.state_to_U(p, st)
     g = md.build_g(p, U, st["e"], w.dt, 1.0, 0.0)
@@ -120,13 +124,14 @@ def test_steps_match_oracle(rhi, name, precond):
         assert max(err.values()) <= TOL_FP64, (step, err, s.stats())
 
 
+@pytest.mark.parametrize("ljac", [1, 2])
 @pytest.mark.parametrize("name", ["lognormal_hhe", "lognormal_hhe_periodic", "uniform_h_ragged"])
-def test_steps_with_dD_dE_match_oracle(rhi, name):
-    """The Newton matrix that keeps dD/dE (BiCGStab on the non-symmetric Schur matrix,
-    preconditioned by the FP32 V-cycle) reaches the same solution as the oracle."""
+def test_steps_with_dD_dE_match_oracle(rhi, name, ljac):
+    """The Newton matrices that keep dD/dE, or are exact (BiCGStab on the non-symmetric Schur
+    matrix, preconditioned by the FP32 V-cycle), reach the same solution as the oracle."""
     w = WL[name]
     s = rhi.solver_for_workload(w, precond=rhi.RHI_PRECOND_MG_FP32, mg_levels=4,
-                                limiter_jacobian=1)
+                                limiter_jacobian=ljac)
     p = oracle_problem(w)
     ref = w.state()
     for step in range(w.nsteps):
