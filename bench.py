@@ -52,16 +52,19 @@ ALU_FLOPS = {
 # kernel has changed since the counters were taken
 TRAFFIC = {}
 # launches bracketed by events inside the timed region
-TIMED_KERNELS = ["cell_residual_schur"]
+TIMED_KERNELS = ["cell_residual_schur", "mg_smooth_f32_fine", "mg_smooth_f64_fine"]
 
 FORM_TEXT = {
-    "plain_fp64": "FP64 Newton/Schur/CG + FP64 multigrid V-cycle (6 levels, 2+2 Jacobi, 16 "
-                  "coarse sweeps), Newton from U^n",
-    "mixed_fp32mg": "FP64 Newton/Schur/CG + FP32 multigrid V-cycle (6 levels, 2+2 Jacobi, 16 "
-                    "coarse sweeps), Newton from U^n",
+    "plain_fp64": "FP64 Newton/Schur/Krylov + FP64 multigrid V-cycle (6 levels, 2+2 Jacobi, "
+                  "16 coarse sweeps), Newton from U^n",
+    "mixed_fp32mg": "FP64 Newton/Schur/Krylov + FP32 multigrid V-cycle (6 levels, 2+2 Jacobi, "
+                    "16 coarse sweeps), Newton from U^n",
     "learned_mixed": "mixed form + learned Newton guess (BF16 tensor-core MLP 9-64-64-64-6, "
                      "falls back to U^n when its ||f|| is larger)",
 }
+NEWTON_TEXT = {0: "Newton matrix with D lagged (symmetric Schur matrix, CG)",
+               1: "Newton matrix with dD/dE kept (BiCGStab)",
+               2: "exact Newton matrix: dD/dE and D's opacity dependence kept (BiCGStab)"}
 
 # algorithmic DRAM bytes per cell of each kernel (H + He; FP64 fields 8 B): the fields each
 # launch must read and write once; stencil neighbours come from cache
@@ -74,6 +77,10 @@ ALG_BYTES = {
     "cg_update_xr": 8 * 4 + 8 * 2,
     "cg_update_p": 8 * 2 + 8,
     "kappa": 8 * 3 + 8,
+    # weighted-Jacobi sweep on the finest level: x, b, diag, 3 lower faces read, x written
+    # (the first sweep of a cycle starts from x = 0 and reads no x): 2 + 2 sweeps average
+    "mg_smooth_f32_fine": (4 * 6 + 3 * 4 * 7) / 4,
+    "mg_smooth_f64_fine": (8 * 6 + 3 * 8 * 7) / 4,
 }
 
 
@@ -356,8 +363,8 @@ def main():
     ap.add_argument("--train-epochs", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--max-newton", type=int, default=200)
-    ap.add_argument("--limiter-jacobian", type=int, default=0,
-                    help="1: keep dD/dE in the Newton matrix (BiCGStab)")
+    ap.add_argument("--limiter-jacobian", type=int, default=2,
+                    help="0: D lagged (CG); 1: dD/dE kept; 2: exact Newton matrix (BiCGStab)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -464,8 +471,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"lognormal_hhe {n}^3 H+He, sigma_ln=1, P(k)~k^-2, {nsrc} sources "
                                "(median 1e49/s), T_B=1e5 K, dt=5e12 s, theta=1, Newton tol "
-                               "1e-8 (u_E = 1e-16), PCG tol 1e-10",
+                               "1e-8 (u_E = 1e-16), Krylov tol 1e-10 relative to ||f||",
                    "form": FORM_TEXT[order[-1]],
+                   "newton_matrix": NEWTON_TEXT[args.limiter_jacobian],
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (~8 GB of fields per form)"},
         "roofline": roof,

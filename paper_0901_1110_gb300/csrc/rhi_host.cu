@@ -305,6 +305,7 @@ int precond_setup(rhi_ctx* h) {
 template <typename T>
 int vcycle(rhi_ctx* h, std::vector<Level<T>>& lv, size_t l, const Op<T>& A0) {
     LinLaunch L(h->st, &h->prof);
+    L.fine_N = h->N;
     Level<T>& v = lv[l];
     const Op<T> A = (l == 0) ? A0 : level_op(h, v);
     const T om = (T)h->prm.mg_omega;

@@ -607,7 +607,8 @@ cudaError_t LinLaunch::axpy(long long N, const double* scal, int slot, const dou
 template <typename T>
 cudaError_t LinLaunch::smooth(const Op<T>& A, const T* b, const T* xin, T* xout, T omega,
                               int first) {
-    begin(sizeof(T) == 4 ? "mg_smooth_f32" : "mg_smooth_f64");
+    if (A.N == fine_N) begin(sizeof(T) == 4 ? "mg_smooth_f32_fine" : "mg_smooth_f64_fine");
+    else begin(sizeof(T) == 4 ? "mg_smooth_f32" : "mg_smooth_f64");
     k_mg_smooth<T><<<stream_blocks(A.N), LIN_BLOCK, 0, st>>>(A, b, xin, xout, omega, first);
     return end();
 }

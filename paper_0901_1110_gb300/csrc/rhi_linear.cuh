@@ -47,6 +47,7 @@ struct LaunchHook {
 struct LinLaunch {
     cudaStream_t st;
     LaunchHook* hook;
+    long long fine_N = -1;      // smoothing sweeps on a level of this size get their own name
     LinLaunch(cudaStream_t s, LaunchHook* h);
     void begin(const char* name);
     cudaError_t end();

@@ -589,9 +589,14 @@ __global__ void __launch_bounds__(256) k_update(const StepParams P, double lam,
 #pragma unroll
     for (int j = 0; j < NS; ++j) n[j] = n0[j * N + c];
     const double E = E0[c], nH = nHa[c];
-    double cap = 1.0;
+    // smallest fraction tau (q + tiny) / (-dq) over the decreasing quantities, kept as a
+    // numerator / denominator pair (denominators > 0) so that one division remains
+    double cnum = 1.0, cden = 1.0;
     auto bound = [&](double q, double dq, double tiny) {
-        if (dq < 0.0) cap = fmin(cap, fmax(P.tau * (q + tiny) / (-dq), 0.0));
+        if (dq < 0.0) {
+            const double num = fmax(P.tau * (q + tiny), 0.0);
+            if (num * cden < cnum * (-dq)) { cnum = num; cden = -dq; }
+        }
     };
     bound(eh[c] + ec, s[0], 0.0);
     bound(E, sEp, 0.0);
@@ -603,6 +608,7 @@ __global__ void __launch_bounds__(256) k_update(const StepParams P, double lam,
         bound(n[2], s[3], 1e-13 * nHe);
         bound(nHe - n[1] - n[2], -s[2] - s[3], 1e-13 * nHe);
     }
+    const double cap = (cden == 1.0) ? cnum : cnum / cden;
     const double fr = fmin(lam, cap);
     ec1[c] = ec + fr * s[0];
     double ksum = 0.0;
