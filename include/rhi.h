@@ -77,6 +77,8 @@ typedef struct {
     int mlp_restart;        /* learned guess: Newton restarts from U^n when the learned start
                                has not converged after this many iterations, or stagnates
                                (||f|| above 0.9 of its value two iterations earlier); 0: never */
+    int mlp_retry;          /* learned guess: after a step whose guess lost to U^n, this many
+                               steps start from U^n without evaluating the network          */
     double growth_max;      /* watchdog line search: a full step may raise ||f|| up to
                                growth_max times the best ||f|| of the step ...               */
     int watchdog;           /* ... for at most this many Newton iterations in a row          */

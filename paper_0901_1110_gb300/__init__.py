@@ -33,7 +33,7 @@ class rhi_params(C.Structure):
                 ("m_grey", C.c_int), ("isothermal", C.c_int), ("limiter", C.c_int),
                 ("kappa_floor", C.c_double), ("u_e", C.c_double), ("u_n", C.c_double),
                 ("u_E", C.c_double), ("tau", C.c_double), ("lam_min", C.c_double),
-                ("mlp_gate", C.c_double), ("mlp_ood", C.c_double), ("mlp_restart", C.c_int), ("growth_max", C.c_double), ("watchdog", C.c_int), ("limiter_jacobian", C.c_int),
+                ("mlp_gate", C.c_double), ("mlp_ood", C.c_double), ("mlp_restart", C.c_int), ("mlp_retry", C.c_int), ("growth_max", C.c_double), ("watchdog", C.c_int), ("limiter_jacobian", C.c_int),
                 ("max_newton", C.c_int), ("max_pcg", C.c_int), ("guess", C.c_int),
                 ("precond", C.c_int), ("mg_levels", C.c_int), ("mg_pre", C.c_int),
                 ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double),

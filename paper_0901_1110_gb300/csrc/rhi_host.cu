@@ -137,6 +137,7 @@ struct rhi_ctx {
     MlpPacked* mlp_pk = nullptr;
     bool mlp_ready = false;
     long long mlp_t = 0;                  // Adam steps taken
+    int mlp_skip = 0;                     // steps left that skip the network (mlp_retry)
     struct Scratch { void* p = nullptr; size_t bytes = 0; };
     Scratch mlp_scr[6];                   // act, del, partials, X, Y, grad staging
     ~rhi_ctx() { for (auto& s : mlp_scr) if (s.p) cudaFree(s.p); }
@@ -169,6 +170,8 @@ int dalloc(rhi_ctx* h, T** p, size_t count) {
 StepParams make_params(const rhi_ctx* h, double dt, double a, double adot) {
     StepParams P{};
     P.nx = h->grid.nx; P.ny = h->grid.ny; P.nz = h->grid.nz;
+    P.fd_nx = make_fastdiv((unsigned)P.nx);
+    P.fd_nxy = make_fastdiv((unsigned)P.nx * (unsigned)P.ny);
     P.N = h->N;
     P.per_x = h->per[0]; P.per_y = h->per[1]; P.per_z = h->per[2];
     P.dx = h->grid.dx;
@@ -269,6 +272,8 @@ template <typename T>
 Op<T> level_op(const rhi_ctx* h, const Level<T>& v) {
     Op<T> A{};
     A.nx = v.nx; A.ny = v.ny; A.nz = v.nz; A.N = v.N;
+    A.fd_nx = make_fastdiv((unsigned)v.nx);
+    A.fd_nxy = make_fastdiv((unsigned)v.nx * (unsigned)v.ny);
     for (int a = 0; a < 3; ++a) { A.per[a] = h->per[a]; A.W[a] = v.W[a]; }
     A.diag = v.diag;
     A.scale = T(1);
@@ -494,6 +499,8 @@ int kappa(rhi_ctx* h, const StepParams& P, const double* n, double* kap) {
 void set_op0(rhi_ctx* h, const StepParams& P, int set, const double* W) {
     Op<double>& A = h->op0;
     A.nx = h->grid.nx; A.ny = h->grid.ny; A.nz = h->grid.nz; A.N = h->N;
+    A.fd_nx = make_fastdiv((unsigned)A.nx);
+    A.fd_nxy = make_fastdiv((unsigned)A.nx * (unsigned)A.ny);
     for (int a = 0; a < 3; ++a) { A.per[a] = h->per[a]; A.W[a] = W + a * h->N; }
     A.diag = h->diag[set];
     A.scale = P.dth;
@@ -502,6 +509,8 @@ void set_op0(rhi_ctx* h, const StepParams& P, int set, const double* W) {
 void set_opns(rhi_ctx* h, const StepParams& P, int set, const double* PQ) {
     OpNS& A = h->opns;
     A.nx = h->grid.nx; A.ny = h->grid.ny; A.nz = h->grid.nz; A.N = h->N;
+    A.fd_nx = make_fastdiv((unsigned)A.nx);
+    A.fd_nxy = make_fastdiv((unsigned)A.nx * (unsigned)A.ny);
     for (int a = 0; a < 3; ++a) {
         A.per[a] = h->per[a];
         A.P[a] = PQ + a * h->N;
@@ -527,7 +536,8 @@ int validate_params(const rhi_params* p) {
     if (!(p->growth_max >= 1.0) || p->watchdog < 0) return 0;
     if (p->max_newton < 0 || p->max_pcg < 1) return 0;
     if (p->guess < 0 || p->guess > RHI_GUESS_LEARNED) return 0;
-    if (!(p->mlp_gate >= 0.0) || !(p->mlp_ood >= 0.0) || p->mlp_restart < 0) return 0;
+    if (!(p->mlp_gate >= 0.0) || !(p->mlp_ood >= 0.0) || p->mlp_restart < 0 || p->mlp_retry < 0)
+        return 0;
     if (p->precond < 0 || p->precond > RHI_PRECOND_MG_FP32) return 0;
     if (p->mg_levels < 1 || p->mg_pre < 1 || p->mg_post < 0 || p->mg_coarse_sweeps < 1) return 0;
     if (p->limiter_jacobian < 0 || p->limiter_jacobian > 2) return 0;
@@ -625,6 +635,7 @@ int rhi_params_default(rhi_params* p, int n_species) {
     p->mlp_gate = 1e-3;
     p->mlp_ood = 6.0;
     p->mlp_restart = 12;
+    p->mlp_retry = 4;
     p->growth_max = 1e3;
     p->watchdog = 3;
     p->limiter_jacobian = 0;
@@ -770,6 +781,7 @@ int rhi_set_state(rhi_handle h, const double* E, const double* e, const double* 
         return fail(h, RHI_ERR_NONPHYSICAL, "rhi_set_state: need E > 0, e > 0, n_H > 0, species >= 0, finite");
     }
     h->have_state = true;
+    h->mlp_skip = 0;
     return RHI_OK;
 }
 
@@ -1002,7 +1014,10 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
         B.diag = h->diag[0]; B.rhs = h->rhs[0]; B.fMt = h->fMt[0]; B.MiU = h->MiU[0];
         if ((rc = cell(h, P, MODE_PREP, B))) return rc;
         if ((rc = residual_norm(h, ncell_blocks(h), &res))) return rc;
-        if (h->prm.guess == RHI_GUESS_LEARNED) {
+        if (h->prm.guess == RHI_GUESS_LEARNED && h->mlp_skip > 0) {
+            h->mlp_skip -= 1;
+            S.guess_used = RHI_GUESS_PREVIOUS;
+        } else if (h->prm.guess == RHI_GUESS_LEARNED) {
             // the network's guess into work iterate 1 with its own Schur set; Newton starts
             // from whichever of U^n and the guess has the smaller ||f||
             MlpArgs A = mlp_args(h, dt, a);
@@ -1027,6 +1042,7 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
                 res = rg;
             } else {
                 S.guess_used = RHI_GUESS_PREVIOUS;
+                h->mlp_skip = h->prm.mlp_retry;
             }
         }
     } else {
@@ -1193,6 +1209,7 @@ int rhi_mlp_set_weights(rhi_handle h, const float* w, size_t n) {
     CK(cudaMemsetAsync(h->mlp_m2, 0, n * sizeof(float), h->st));
     CK(cudaMemsetAsync(h->mlp_g, 0, n * sizeof(float), h->st));
     h->mlp_t = 0;
+    h->mlp_skip = 0;
     if ((rc = mlp_repack(h))) return rc;
     h->mlp_ready = true;
     return RHI_OK;

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "rhi.h"
+#include "rhi_fastdiv.h"
 
 namespace rhi {
 
@@ -40,6 +41,7 @@ std::vector<double2> build_rate_table();
 struct StepParams {
     int nx, ny, nz;
     long long N;
+    FastDiv fd_nx, fd_nxy;            // division by nx and nx * ny
     int per_x, per_y, per_z;          // periodic axes
     double dx;
     double a, ia3, adot_a;            // a, 1/a^3, adot / a
@@ -68,11 +70,13 @@ struct Nbr {
 
 __device__ __forceinline__ void cell_coords(const StepParams& P, long long c, int& i, int& j,
                                             int& k) {
-    long long nxy = (long long)P.nx * P.ny;
-    k = (int)(c / nxy);
-    long long r = c - (long long)k * nxy;
-    j = (int)(r / P.nx);
-    i = (int)(r - (long long)j * P.nx);
+    const unsigned cu = (unsigned)c;
+    const unsigned kk = fdiv(cu, P.fd_nxy);
+    const unsigned r = cu - kk * P.fd_nxy.d;
+    const unsigned jj = fdiv(r, P.fd_nx);
+    k = (int)kk;
+    j = (int)jj;
+    i = (int)(r - jj * P.fd_nx.d);
 }
 
 __device__ __forceinline__ Nbr neighbours(const StepParams& P, long long c, int i, int j, int k) {

@@ -19,11 +19,25 @@ int stream_blocks(long long N) {
 
 template <typename T>
 __device__ __forceinline__ void coords3(const Op<T>& A, long long c, int& i, int& j, int& k) {
-    const long long nxy = (long long)A.nx * A.ny;
-    k = (int)(c / nxy);
-    const long long r = c - (long long)k * nxy;
-    j = (int)(r / A.nx);
-    i = (int)(r - (long long)j * A.nx);
+    const unsigned cu = (unsigned)c;
+    const unsigned kk = fdiv(cu, A.fd_nxy);
+    const unsigned r = cu - kk * A.fd_nxy.d;
+    const unsigned jj = fdiv(r, A.fd_nx);
+    k = (int)kk;
+    j = (int)jj;
+    i = (int)(r - jj * A.fd_nx.d);
+}
+
+// coordinates of index c on an nx x ny x nz grid given the dividers of nx and nx * ny
+__device__ __forceinline__ void coords_fd(long long c, const FastDiv& fx, const FastDiv& fxy,
+                                          int& i, int& j, int& k) {
+    const unsigned cu = (unsigned)c;
+    const unsigned kk = fdiv(cu, fxy);
+    const unsigned r = cu - kk * fxy.d;
+    const unsigned jj = fdiv(r, fx);
+    k = (int)kk;
+    j = (int)jj;
+    i = (int)(r - jj * fx.d);
 }
 
 // (A x)_c with the six neighbours of c
@@ -156,9 +170,15 @@ constexpr int RED_BLOCK = 1024;
 __global__ void __launch_bounds__(RED_BLOCK) k_reduce(const double* __restrict__ partials, int n,
                                                       double* __restrict__ scal, int op,
                                                       int slot) {
-    double acc = 0.0;
-    for (int q = threadIdx.x; q < n; q += RED_BLOCK) acc += partials[q];
+    // the BiCGStab updates carry a second set of partials after the first n
+    const bool two = op == RED_BICG_OMEGA || op == RED_BICG_RHO;
+    double acc = 0.0, acc2 = 0.0;
+    for (int q = threadIdx.x; q < n; q += RED_BLOCK) {
+        acc += partials[q];
+        if (two) acc2 += partials[n + q];
+    }
     const double s = block_sum<RED_BLOCK>(acc);
+    const double s2 = two ? block_sum<RED_BLOCK>(acc2) : 0.0;
     if (threadIdx.x == 0) {
         if (op == RED_SUM) {
             scal[slot] = s;
@@ -174,15 +194,13 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce(const double* __restrict__
             if (!(s != 0.0)) scal[S_BREAK] = 1.0;
             scal[S_ALPHA] = (s != 0.0) ? scal[S_RHO] / s : 0.0;
         } else if (op == RED_BICG_OMEGA) {          // partials: t.s then t.t
-            double tt = 0.0;
-            for (int q = 0; q < n; ++q) tt += partials[n + q];
+            const double tt = s2;
             scal[S_TS] = s;
             scal[S_TT] = tt;
             scal[S_OMEGA] = (tt > 0.0) ? s / tt : 0.0;
             if (!(tt > 0.0)) scal[S_BREAK] = 1.0;
         } else {                                    // RED_BICG_RHO: partials r.r then rh.r
-            double rho = 0.0;
-            for (int q = 0; q < n; ++q) rho += partials[n + q];
+            const double rho = s2;
             scal[S_RR] = s;
             scal[S_BETA] = (rho / scal[S_RHO]) * (scal[S_ALPHA] / scal[S_OMEGA]);
             scal[S_RHO] = rho;
@@ -204,9 +222,8 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_matvec_ns(const OpNS A, const dou
     const long long sz = (long long)A.nx * A.ny;
     for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < A.N;
          c += (long long)gridDim.x * LIN_BLOCK) {
-        const int k = (int)(c / sz);
-        const long long rem = c - (long long)k * sz;
-        const int j = (int)(rem / A.nx), i = (int)(rem - (long long)j * A.nx);
+        int i, j, k;
+        coords_fd(c, A.fd_nx, A.fd_nxy, i, j, k);
         const int q[3] = {i, j, k};
         const int n[3] = {A.nx, A.ny, A.nz};
         const long long s[3] = {1, A.nx, sz};
@@ -346,14 +363,13 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_smooth(const Op<T> A, const T*
 template <typename T>
 __global__ void __launch_bounds__(LIN_BLOCK) k_mg_restrict(const Op<T> A, const T* __restrict__ b,
                                                            const T* __restrict__ x, int cnx,
-                                                           int cny, int cnz,
-                                                           T* __restrict__ bc) {
+                                                           int cny, int cnz, FastDiv fcx,
+                                                           FastDiv fcxy, T* __restrict__ bc) {
     const long long Nc = (long long)cnx * cny * cnz;
     for (long long cc = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; cc < Nc;
          cc += (long long)gridDim.x * LIN_BLOCK) {
-        const int K = (int)(cc / ((long long)cnx * cny));
-        const long long rem = cc - (long long)K * cnx * cny;
-        const int J = (int)(rem / cnx), I = (int)(rem - (long long)J * cnx);
+        int I, J, K;
+        coords_fd(cc, fcx, fcxy, I, J, K);
         T acc = T(0);
         int cnt = 0;
         for (int dk = 0; dk < 2; ++dk) {
@@ -378,14 +394,14 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_restrict(const Op<T> A, const 
 // x_f += x_c(parent)
 template <typename T>
 __global__ void __launch_bounds__(LIN_BLOCK) k_mg_prolong(int nx, int ny, int nz, int cnx, int cny,
+                                                          FastDiv fx, FastDiv fxy,
                                                           const T* __restrict__ xc,
                                                           T* __restrict__ xf) {
     const long long N = (long long)nx * ny * nz;
     for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
          c += (long long)gridDim.x * LIN_BLOCK) {
-        const int k = (int)(c / ((long long)nx * ny));
-        const long long rem = c - (long long)k * nx * ny;
-        const int j = (int)(rem / nx), i = (int)(rem - (long long)j * nx);
+        int i, j, k;
+        coords_fd(c, fx, fxy, i, j, k);
         xf[c] += xc[(i >> 1) + (long long)cnx * ((j >> 1) + (long long)cny * (k >> 1))];
     }
 }
@@ -617,14 +633,14 @@ cudaError_t LinLaunch::restrict_res(const Op<T>& A, const T* b, const T* x, int 
                                     int cnz, T* bc) {
     begin(sizeof(T) == 4 ? "mg_restrict_f32" : "mg_restrict_f64");
     k_mg_restrict<T><<<stream_blocks((long long)cnx * cny * cnz), LIN_BLOCK, 0, st>>>(
-        A, b, x, cnx, cny, cnz, bc);
+        A, b, x, cnx, cny, cnz, make_fastdiv((unsigned)cnx), make_fastdiv((unsigned)cnx * cny), bc);
     return end();
 }
 template <typename T>
 cudaError_t LinLaunch::prolong(int nx, int ny, int nz, int cnx, int cny, const T* xc, T* xf) {
     begin(sizeof(T) == 4 ? "mg_prolong_f32" : "mg_prolong_f64");
-    k_mg_prolong<T><<<stream_blocks((long long)nx * ny * nz), LIN_BLOCK, 0, st>>>(nx, ny, nz, cnx,
-                                                                                cny, xc, xf);
+    k_mg_prolong<T><<<stream_blocks((long long)nx * ny * nz), LIN_BLOCK, 0, st>>>(
+        nx, ny, nz, cnx, cny, make_fastdiv((unsigned)nx), make_fastdiv((unsigned)nx * ny), xc, xf);
     return end();
 }
 template <typename TF, typename TC>

@@ -10,6 +10,7 @@ template <typename T>
 struct Op {
     int nx, ny, nz;
     long long N;
+    FastDiv fd_nx, fd_nxy;
     int per[3];
     const T* diag;
     const T* W[3];       // lower-face coefficient per axis (0 on zero-flux boundary faces)
@@ -21,6 +22,7 @@ struct Op {
 struct OpNS {
     int nx, ny, nz;
     long long N;
+    FastDiv fd_nx, fd_nxy;
     int per[3];
     const double* diag;
     const double* P[3];

@@ -23,25 +23,31 @@ constexpr int TRAIN_BLOCK = 128;
 // ------------------------------------------------------------------------------------------
 // features of one cell (FP32 from the FP64 state)
 
+__device__ __forceinline__ float log10_clamped(double x) {
+    // FP32 logarithm of a positive ratio formed in FP64, clamped into the FP32 range
+    return log10f(fminf(fmaxf((float)x, 1e-37f), 1e37f));
+}
+
 __device__ __forceinline__ void cell_features(const MlpArgs& A, long long c, float (&f)[MLP_IN]) {
-    // logarithms in FP64 (once per cell and step): the source ratio 4 pi eta dt / E and the
-    // field can leave the FP32 range in cells the radiation has not reached yet
+    // ratios in FP64 (the source ratio and the field leave the FP32 range in cells the
+    // radiation has not reached), logarithms in FP32
     const double E = A.E[c], e = A.e[c], nH = A.nH[c];
-    const double nHe = A.y_he * nH;
-    f[0] = (float)log10(E * A.iu_E);
-    f[1] = (float)log10(e * A.iu_e);
-    f[2] = (float)log10(fmax(A.n[c] / nH, 1e-30));
+    const double inH = 1.0 / nH;
+    f[0] = log10_clamped(E * A.iu_E);
+    f[1] = log10_clamped(e * A.iu_e);
+    f[2] = log10_clamped(fmax(A.n[c] * inH, 1e-30));
     if (A.ns == 3) {
-        f[3] = (float)log10(fmax(A.n[A.N + c] / nHe, 1e-30));
-        f[4] = (float)log10(fmax(A.n[2 * A.N + c] / nHe, 1e-30));
+        const double inHe = inH / A.y_he;
+        f[3] = log10_clamped(fmax(A.n[A.N + c] * inHe, 1e-30));
+        f[4] = log10_clamped(fmax(A.n[2 * A.N + c] * inHe, 1e-30));
     } else {
         f[3] = 0.0f;
         f[4] = 0.0f;
     }
-    f[5] = (float)log10(nH * A.iu_n);
-    f[6] = (float)log10(A.dt * A.gam_per_E * E + 1e-30);
-    f[7] = (float)log10(1.0 + A.src[c] * A.dt / E);
-    f[8] = (float)log10(A.dt * 1e-12);
+    f[5] = log10_clamped(nH * A.iu_n);
+    f[6] = log10_clamped(A.dt * A.gam_per_E * E + 1e-30);
+    f[7] = log10f(1.0f + fminf((float)(A.src[c] * A.dt / E), 1e37f));
+    f[8] = log10_clamped(A.dt * 1e-12);
 }
 
 __global__ void k_mlp_features(const MlpArgs A, float* __restrict__ X) {
@@ -205,26 +211,28 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_mlp_infer(const MlpArgs A,
 #pragma unroll
                 for (int q = 0; q < MLP_OUT; ++q) Y[c * MLP_OUT + q] = o[q];
             } else {
-                // decode; cells whose predicted change stays below the gate keep U^n
+                // decode (FP32 transcendentals; the logit of the old fraction in FP64, where
+                // neutral cells sit within 1e-16 of 1); cells whose predicted change stays
+                // below the gate, or whose inputs left the training range, keep U^n
                 const double E0 = A.E[c], e0 = A.e[c], nH = A.nH[c];
                 const double x0 = fmin(fmax(A.n[c] / nH, 1e-30), 1.0 - 1e-16);
                 float change = fmaxf(fabsf(o[0]), fabsf(o[1]));
                 change = fmaxf(change, fabsf(o[2] - (float)(log(x0) - log1p(-x0))));
-                const double xHI = 1.0 / (1.0 + exp(-(double)o[2]));
+                const double xHI = 1.0 / (1.0 + (double)expf(-o[2]));
                 double nHeI = 0.0, nHeII = 0.0;
                 if (A.ns == 3) {
-                    // softmax in FP64: n_HeI + n_HeII stays below n_He to rounding, so the
-                    // derived n_HeIII of the guess is not negative beyond the positivity cap's
-                    // tolerance (an FP32 softmax can overshoot by 1e-7 n_He and freeze the cell)
+                    // softmax normalised in FP64: n_HeI + n_HeII stays below n_He to rounding,
+                    // so the derived n_HeIII of the guess is not negative beyond the positivity
+                    // cap's tolerance (an FP32 sum can overshoot by 1e-7 n_He and freeze the cell)
                     const double nHe = A.y_he * nH;
-                    const double mx = fmax((double)o[3], fmax((double)o[4], (double)o[5]));
-                    const double z0 = exp(o[3] - mx), z1 = exp(o[4] - mx), z2 = exp(o[5] - mx);
+                    const float mx = fmaxf(o[3], fmaxf(o[4], o[5]));
+                    const double z0 = expf(o[3] - mx), z1 = expf(o[4] - mx), z2 = expf(o[5] - mx);
                     const double iz = 1.0 / (z0 + z1 + z2);
                     const double f0 = A.n[A.N + c] / nHe, f1 = A.n[2 * A.N + c] / nHe;
                     const double f2 = 1.0 - f0 - f1;
-                    change = fmaxf(change, fabsf((float)(log(fmax(z0 * iz, 1e-30)) - log(fmax(f0, 1e-30)))));
-                    change = fmaxf(change, fabsf((float)(log(fmax(z1 * iz, 1e-30)) - log(fmax(f1, 1e-30)))));
-                    change = fmaxf(change, fabsf((float)(log(fmax(z2 * iz, 1e-30)) - log(fmax(f2, 1e-30)))));
+                    change = fmaxf(change, fabsf(logf((float)fmax(z0 * iz, 1e-30)) - logf((float)fmax(f0, 1e-30))));
+                    change = fmaxf(change, fabsf(logf((float)fmax(z1 * iz, 1e-30)) - logf((float)fmax(f1, 1e-30))));
+                    change = fmaxf(change, fabsf(logf((float)fmax(z2 * iz, 1e-30)) - logf((float)fmax(f2, 1e-30))));
                     nHeI = nHe * (z0 * iz);
                     nHeII = nHe * (z1 * iz);
                 }
@@ -235,13 +243,13 @@ __global__ void __launch_bounds__(32 * INF_WARPS) k_mlp_infer(const MlpArgs A,
                     for (int s = 0; s < A.ns; ++s) U[(1 + s) * N + c] = A.n[s * N + c];
                     U[(1 + A.ns) * N + c] = E0;
                 } else {
-                    U[c] = A.isothermal ? 0.0 : e0 * expm1(2.302585092994046 * (double)o[1]);
+                    U[c] = A.isothermal ? 0.0 : e0 * (double)expm1f(2.302585093f * o[1]);
                     U[N + c] = nH * xHI;
                     if (A.ns == 3) {
                         U[2 * N + c] = nHeI;
                         U[3 * N + c] = nHeII;
                     }
-                    U[(1 + A.ns) * N + c] = E0 * exp(2.302585092994046 * (double)o[0]);
+                    U[(1 + A.ns) * N + c] = E0 * (double)exp10f(o[0]);
                 }
             }
         }

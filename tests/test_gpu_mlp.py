@@ -160,7 +160,7 @@ def test_learned_guess_reaches_the_same_root(rhi, trained):
     """The implicit step started from the network's guess converges to the oracle's Newton
     solution (started from U^n, exact linear solves)."""
     w = trained["workload"]
-    s = rhi.solver_for_workload(w, guess=rhi.RHI_GUESS_LEARNED, mlp_restart=0)
+    s = rhi.solver_for_workload(w, guess=rhi.RHI_GUESS_LEARNED, mlp_restart=0, mlp_retry=0)
     s.mlp_set_weights(trained["w"])
     p = oracle_problem(w)
     ref = w.state()
@@ -269,12 +269,14 @@ def test_decoded_guess_matches_oracle_decode(rhi, trained):
               keep(gate + 1e-4, ood * (1 - 1e-4) if ood > 0 else 0.0))
         assert ok.mean() > 0.95
         eh = np.asarray(st["e"]).ravel()
-        np.testing.assert_allclose((eh + G[0])[ok], ref["e"][ok], rtol=1e-12)
-        np.testing.assert_allclose(G[1 + p.ns][ok], ref["E"][ok], rtol=1e-12)
+        # the decode's exponentials run in FP32 (relative error a few 1e-7); the guess only
+        # starts Newton, whose root does not depend on it
+        np.testing.assert_allclose((eh + G[0])[ok], ref["e"][ok], rtol=2e-6)
+        np.testing.assert_allclose(G[1 + p.ns][ok], ref["E"][ok], rtol=2e-6)
         nref = np.asarray(ref["n"]).reshape(p.ns, -1)
         for X_ in range(p.ns):
-            np.testing.assert_allclose(G[1 + X_][ok], nref[X_][ok], rtol=1e-12,
-                                       atol=1e-15 * p.nH.max())
+            np.testing.assert_allclose(G[1 + X_][ok], nref[X_][ok], rtol=2e-6,
+                                       atol=1e-12 * p.nH.max())
         assert np.all(G[1 + p.ns] > 0) and np.all(eh + G[0] > 0)
         if ood == 2.0:
             assert mask.any()
@@ -302,3 +304,23 @@ def test_residual_at_an_iterate_matches_oracle(rhi):
         scale = np.abs(fr).max()
         assert np.abs(f - fr).max() <= 1e-10 * scale
         assert abs(nrm / md.rms_norm(p, fr * p.scales()[:, None]) - 1) < 1e-10
+
+
+def test_rejected_guess_skips_the_network_for_mlp_retry_steps(rhi):
+    """An untrained network's guess loses to U^n; the next mlp_retry steps start from U^n
+    without evaluating it, and the step after that tries it again."""
+    w = _workload(7, shape=(10, 11, 12), nsteps=4)
+    s = rhi.solver_for_workload(w, guess=rhi.RHI_GUESS_LEARNED, mlp_retry=2, mlp_gate=0.0,
+                                mlp_ood=0.0)
+    rng = np.random.default_rng(5)
+    wts = om.init_weights(9)
+    d = om.unpack(wts)
+    d["b4"] = rng.normal(0.0, 3.0, om.NOUT)           # large random changes: a bad guess
+    s.mlp_set_weights(om.pack(d).astype(np.float32))
+    tried = []
+    for _ in range(4):
+        s.step(w.dt, newton_tol=1e-10, lin_tol=1e-10)
+        st = s.stats()
+        assert st["guess_used"] == rhi.RHI_GUESS_PREVIOUS
+        tried.append(st["res_guess_prev"] > 0)
+    assert tried == [True, False, False, True], tried
