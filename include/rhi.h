@@ -95,6 +95,8 @@ typedef struct {
     int mg_pre, mg_post;    /* weighted-Jacobi sweeps before / after the coarse correction   */
     int mg_coarse_sweeps;   /* weighted-Jacobi sweeps on the coarsest level                  */
     double mg_omega;        /* Jacobi weight                                                 */
+    int vcycle_graph;       /* 1: the FP32 V-cycle is captured once as a CUDA graph and
+                               replayed (on a library-owned stream ordered by events)       */
     /* grey constants per absorber (HI, HeI, HeII) of eq. adaptive_spectrum:
        kappa = sum sk_X n_X / a^3, Gamma_X = c pgam_X E / a^3, G = c E sum ph_X n_X / (a^3 rho) */
     double sk[3], pgam[3], ph[3];

@@ -36,7 +36,7 @@ class rhi_params(C.Structure):
                 ("mlp_gate", C.c_double), ("mlp_ood", C.c_double), ("mlp_restart", C.c_int), ("mlp_retry", C.c_int), ("growth_max", C.c_double), ("watchdog", C.c_int), ("limiter_jacobian", C.c_int),
                 ("max_newton", C.c_int), ("max_pcg", C.c_int), ("guess", C.c_int),
                 ("precond", C.c_int), ("mg_levels", C.c_int), ("mg_pre", C.c_int),
-                ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double),
+                ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double), ("vcycle_graph", C.c_int),
                 ("sk", C.c_double * 3), ("pgam", C.c_double * 3), ("ph", C.c_double * 3),
                 ("photon_energy", C.c_double)]
 

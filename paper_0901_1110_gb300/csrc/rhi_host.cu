@@ -131,6 +131,17 @@ struct rhi_ctx {
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
+    // the FP32 V-cycle captured as a CUDA graph
+    struct VGraph {
+        cudaGraphExec_t exec = nullptr;
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        double scale = 0.0;
+        std::vector<float*> post;       // level buffers (x, xt) after the captured cycle
+        int kernels = 0;
+        bool failed = false;
+    } vg;
+
     // learned guess: FP32 master weights, Adam moments, gradient, BF16 inference copy;
     // scratch of the training / inspection entry points grows on demand
     float *mlp_w = nullptr, *mlp_m1 = nullptr, *mlp_m2 = nullptr, *mlp_g = nullptr;
@@ -188,6 +199,12 @@ StepParams make_params(const rhi_ctx* h, double dt, double a, double adot) {
     P.y_he = h->prm.y_he;
     P.u_e = h->prm.u_e; P.u_n = h->prm.u_n; P.u_E = h->prm.u_E;
     P.iu_e = 1.0 / P.u_e; P.iu_n = 1.0 / P.u_n; P.iu_E = 1.0 / P.u_E;
+    P.sc_ne = P.dth * P.u_n * P.iu_e;
+    P.sc_en = P.dth * P.u_e * P.iu_n;
+    P.sc_Ee = P.dth * P.u_E * P.iu_e;
+    P.sc_En = P.dth * P.u_E * P.iu_n;
+    P.sc_eE = P.dth * P.u_e * P.iu_E;
+    P.sc_nE = P.dth * P.u_n * P.iu_E;
     for (int X = 0; X < 3; ++X) { P.sk[X] = h->prm.sk[X]; P.pg[X] = h->prm.pgam[X]; P.ph[X] = h->prm.ph[X]; }
     P.tau = h->prm.tau;
     P.table = h->table;
@@ -308,8 +325,10 @@ int precond_setup(rhi_ctx* h) {
 
 // one V-cycle on levels l.. with right-hand side lv[l].b; result in lv[l].x
 template <typename T>
-int vcycle(rhi_ctx* h, std::vector<Level<T>>& lv, size_t l, const Op<T>& A0) {
-    LinLaunch L(h->st, &h->prof);
+int vcycle(rhi_ctx* h, std::vector<Level<T>>& lv, size_t l, const Op<T>& A0,
+           cudaStream_t st = nullptr, LaunchHook* hook = nullptr) {
+    if (!hook) { st = h->st; hook = &h->prof; }
+    LinLaunch L(st, hook);
     L.fine_N = h->N;
     Level<T>& v = lv[l];
     const Op<T> A = (l == 0) ? A0 : level_op(h, v);
@@ -329,13 +348,88 @@ int vcycle(rhi_ctx* h, std::vector<Level<T>>& lv, size_t l, const Op<T>& A0) {
     }
     Level<T>& c = lv[l + 1];
     CK(L.restrict_res<T>(A, v.b, v.x, c.nx, c.ny, c.nz, c.b));
-    int rc = vcycle<T>(h, lv, l + 1, A0);
+    int rc = vcycle<T>(h, lv, l + 1, A0, st, hook);
     if (rc) return rc;
-    CK(L.prolong<T>(v.nx, v.ny, v.nz, c.nx, c.ny, c.x, v.x));
-    for (int s = 0; s < h->prm.mg_post; ++s) {
+    if (h->prm.mg_post == 0) {
+        CK(L.prolong<T>(v.nx, v.ny, v.nz, c.nx, c.ny, c.x, v.x));
+        return RHI_OK;
+    }
+    CK(L.smooth_prolong<T>(A, v.b, v.x, c.x, c.nx, c.ny, v.xt, om));      // prolong + sweep
+    std::swap(v.x, v.xt);
+    for (int s = 1; s < h->prm.mg_post; ++s) {
         CK(L.smooth<T>(A, v.b, v.x, v.xt, om, 0));
         std::swap(v.x, v.xt);
     }
+    return RHI_OK;
+}
+
+// ---- the FP32 V-cycle as a CUDA graph
+//
+// One V-cycle is about 45 launches, most of them on grids of 64^3 cells and below, where the
+// launch gap is longer than the kernel.  The cycle is captured once (on a private stream) and
+// replayed as one graph launch ordered after / before the handle's stream by events.  The
+// graph binds the level buffers and the operator's scale (dt theta) at capture; it is
+// captured again when the scale changes or the host's view of the ping-pong buffers no longer
+// matches the state after capture (a direct V-cycle ran in between).
+
+struct Counter : LaunchHook {
+    int n = 0;
+    void begin(const char*) override { ++n; }
+    void end() override {}
+};
+
+bool vcycle_graph_usable(const rhi_ctx* h) {
+    if (!h->prm.vcycle_graph || h->vg.failed) return false;
+    if (!h->prof.on) return true;
+    // per-launch timing of a V-cycle kernel needs the direct launches
+    if (h->prof.only.empty()) return false;
+    for (const auto& nm : h->prof.only)
+        if (nm.compare(0, 3, "mg_") == 0) return false;
+    return true;
+}
+
+int vcycle_graph(rhi_ctx* h, const Op<float>& A0) {
+    auto& lv = h->mg32;
+    auto& g = h->vg;
+    bool valid = g.exec && g.scale == (double)A0.scale && g.post.size() == 2 * lv.size();
+    for (size_t l = 0; valid && l < lv.size(); ++l)
+        valid = g.post[2 * l] == lv[l].x && g.post[2 * l + 1] == lv[l].xt;
+    if (!valid) {
+        if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+        if (!g.st) {
+            CK(cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&g.ev0, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&g.ev1, cudaEventDisableTiming));
+        }
+        Counter cnt;
+        CK(cudaStreamBeginCapture(g.st, cudaStreamCaptureModeThreadLocal));
+        int rc = vcycle<float>(h, lv, 0, A0, g.st, &cnt);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(g.st, &graph);
+        if (rc || e != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            g.failed = true;
+            return rc ? rc : fail(h, RHI_ERR_CUDA, std::string("V-cycle capture: ") + cudaGetErrorString(e));
+        }
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g.failed = true;
+            g.exec = nullptr;
+            return fail(h, RHI_ERR_CUDA, std::string("V-cycle graph: ") + cudaGetErrorString(e));
+        }
+        g.kernels = cnt.n;
+        g.scale = (double)A0.scale;
+        g.post.clear();
+        for (auto& v : lv) { g.post.push_back(v.x); g.post.push_back(v.xt); }
+    }
+    Scope s(h->prof, "mg_vcycle_graph");
+    CK(cudaEventRecord(g.ev0, h->st));
+    CK(cudaStreamWaitEvent(g.st, g.ev0, 0));
+    CK(cudaGraphLaunch(g.exec, g.st));
+    CK(cudaEventRecord(g.ev1, g.st));
+    CK(cudaStreamWaitEvent(h->st, g.ev1, 0));
+    h->prof.launches += g.kernels - 1;      // the scope counted one
     return RHI_OK;
 }
 
@@ -362,7 +456,7 @@ int precond_apply(rhi_ctx* h, const double* r, double** zout, int& nparts) {
         auto& lv = h->mg32;
         CK(L.to_f32(N, r, lv[0].b));
         Op<float> A0 = level_op(h, lv[0]);
-        int rc = vcycle<float>(h, lv, 0, A0);
+        int rc = vcycle_graph_usable(h) ? vcycle_graph(h, A0) : vcycle<float>(h, lv, 0, A0);
         if (rc) return rc;
         CK(L.from_f32_dot(N, lv[0].x, r, h->z, h->partials, nparts));
         *zout = h->z;
@@ -542,6 +636,7 @@ int validate_params(const rhi_params* p) {
     if (p->mg_levels < 1 || p->mg_pre < 1 || p->mg_post < 0 || p->mg_coarse_sweeps < 1) return 0;
     if (p->limiter_jacobian < 0 || p->limiter_jacobian > 2) return 0;
     if (!(p->mg_omega > 0.0 && p->mg_omega <= 1.0)) return 0;
+    if (p->vcycle_graph != 0 && p->vcycle_graph != 1) return 0;
     return 1;
 }
 
@@ -647,7 +742,8 @@ int rhi_params_default(rhi_params* p, int n_species) {
     p->mg_pre = 2;
     p->mg_post = 2;
     p->mg_coarse_sweeps = 16;
-    p->mg_omega = 0.8;
+    p->mg_omega = 0.9;
+    p->vcycle_graph = 1;
     return rhi_grey_constants(RHI_SPECTRUM_MONO, 13.6 * EV, n_species, p->sk, p->pgam, p->ph,
                               &p->photon_energy);
 }
@@ -732,6 +828,11 @@ void rhi_destroy(rhi_handle h) {
     if (h->h_scal) cudaFreeHost(h->h_scal);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->vg.st) cudaStreamSynchronize(h->vg.st);
+    if (h->vg.exec) cudaGraphExecDestroy(h->vg.exec);
+    if (h->vg.ev0) cudaEventDestroy(h->vg.ev0);
+    if (h->vg.ev1) cudaEventDestroy(h->vg.ev1);
+    if (h->vg.st) cudaStreamDestroy(h->vg.st);
     delete h;
 }
 

@@ -55,6 +55,9 @@ struct StepParams {
     int limiter_newton;               // 1: keep dD/dE in the Newton matrix (non-symmetric S)
     double y_he;
     double u_e, u_n, u_E, iu_e, iu_n, iu_E;
+    // dt theta times ratios of scalings for the scaled local blocks: M[0][s>0] (u_n / u_e),
+    // M[r>0][0] (u_e / u_n), U column (u_E / u_e, u_E / u_n), L row (u_e / u_E, u_n / u_E)
+    double sc_ne, sc_en, sc_Ee, sc_En, sc_eE, sc_nE;
     double sk[3], pg[3], ph[3];
     double tau;
     const double2* __restrict__ table;

@@ -82,6 +82,9 @@ struct LinLaunch {
     template <typename T>
     cudaError_t smooth(const Op<T>& A, const T* b, const T* xin, T* xout, T omega, int first);
     template <typename T>
+    cudaError_t smooth_prolong(const Op<T>& A, const T* b, const T* xin, const T* xc, int cnx,
+                               int cny, T* xout, T omega);
+    template <typename T>
     cudaError_t restrict_res(const Op<T>& A, const T* b, const T* x, int cnx, int cny, int cnz,
                              T* bc);
     template <typename T>

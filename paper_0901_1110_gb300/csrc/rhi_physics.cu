@@ -494,13 +494,6 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const P
 #pragma unroll
             for (int v = 0; v < NV; ++v) B.U0[v * N + c] = U[v] + cap * d[v];
         } else {
-            // scalings of the local unknowns (e_c, n_1 ..) and their inverses
-            double us[NM], ius[NM];
-#pragma unroll
-            for (int r = 0; r < NM; ++r) {
-                us[r] = r == 0 ? P.u_e : P.u_n;
-                ius[r] = r == 0 ? P.iu_e : P.iu_n;
-            }
             // scaled residual (eq. nonlinear_residual / eq. scalings)
             double fs[NV];
 #pragma unroll
@@ -510,15 +503,17 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const P
                 fsq += fs[v] * fs[v];
                 if (B.f_out) B.f_out[v * N + c] = fs[v];
             }
-            // scaled local blocks (eq. schur_components)
+            // scaled local blocks (eq. schur_components); dt theta u_s / u_r products per step
             double M[NM][NM], y[NM], z[NM], Lr[NM];
 #pragma unroll
             for (int r = 0; r < NM; ++r) {
 #pragma unroll
-                for (int s = 0; s < NM; ++s)
-                    M[r][s] = (r == s ? 1.0 : 0.0) + P.dth * lo.dLx[r][s] * us[s] * ius[r];
-                z[r] = P.dth * lo.dLxE[r] * P.u_E * ius[r];
-                Lr[r] = P.dth * lo.dLEx[r] * us[r] * P.iu_E;
+                for (int s = 0; s < NM; ++s) {
+                    const double sc = (r == 0) == (s == 0) ? P.dth : (r == 0 ? P.sc_ne : P.sc_en);
+                    M[r][s] = (r == s ? 1.0 : 0.0) + lo.dLx[r][s] * sc;
+                }
+                z[r] = lo.dLxE[r] * (r == 0 ? P.sc_Ee : P.sc_En);
+                Lr[r] = lo.dLEx[r] * (r == 0 ? P.sc_eE : P.sc_nE);
                 y[r] = fs[r];
             }
             const double Dloc = 1.0 + P.dth * lo.dLEE;
