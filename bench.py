@@ -79,13 +79,9 @@ ALG_BYTES = {
     "cg_update_p": 8 * 2 + 8,
     "kappa": 8 * 3 + 8,
     # weighted-Jacobi sweep on the finest level: x, b, diag, 3 lower faces read, x written
-    # (the first sweep of a cycle starts from x = 0 and reads no x); with 2 + 2 sweeps the
-    # first post-sweep carries the prolongation under its own name, so three plain sweeps
-    # (one from x = 0) remain per cycle
-    "mg_smooth_f32_fine": (4 * 6 + 2 * 4 * 7) / 3,
-    "mg_smooth_f64_fine": (8 * 6 + 2 * 8 * 7) / 3,
-    "mg_smooth_prolong_f32_fine": 4 * 7 + 4 / 8,
-    "mg_smooth_prolong_f64_fine": 8 * 7 + 8 / 8,
+    # (the first sweep of a cycle starts from x = 0 and reads no x): 2 + 2 sweeps average
+    "mg_smooth_f32_fine": (4 * 6 + 3 * 4 * 7) / 4,
+    "mg_smooth_f64_fine": (8 * 6 + 3 * 8 * 7) / 4,
 }
 
 

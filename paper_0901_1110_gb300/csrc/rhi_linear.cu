@@ -359,45 +359,30 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_smooth(const Op<T> A, const T*
     }
 }
 
-// prolongation fused into the first post-smoothing sweep: the sweep reads x + P xc at the cell
-// and its six neighbours (P = injection from the parent cell) and writes the smoothed,
-// corrected iterate, which saves the separate read-modify-write pass of the prolongation
+// all Jacobi sweeps of the coarsest level in one CTA: the same arithmetic as that many
+// k_mg_smooth launches (first sweep from x = 0 into x, then x and xt alternate), with a block
+// barrier in place of each kernel boundary
+constexpr int COARSE_BLOCK = 1024;
 template <typename T>
-__global__ void __launch_bounds__(LIN_BLOCK) k_mg_smooth_prolong(const Op<T> A,
-                                                                 const T* __restrict__ b,
-                                                                 const T* __restrict__ xin,
-                                                                 const T* __restrict__ xc,
-                                                                 int cnx, int cny,
-                                                                 T* __restrict__ xout, T omega) {
-    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < A.N;
-         c += (long long)gridDim.x * LIN_BLOCK) {
-        int q[3];
-        coords3(A, c, q[0], q[1], q[2]);
-        auto parent = [&](int i, int j, int k) {
-            return xc[(i >> 1) + (long long)cnx * ((j >> 1) + (long long)cny * (k >> 1))];
-        };
-        const T x0 = xin[c] + parent(q[0], q[1], q[2]);
-        const int n[3] = {A.nx, A.ny, A.nz};
-        const long long s[3] = {1, A.nx, (long long)A.nx * A.ny};
-        T off = T(0);
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-            int r[3] = {q[0], q[1], q[2]};
-            if (q[ax] > 0 || A.per[ax]) {
-                const bool wrap = q[ax] == 0;
-                r[ax] = wrap ? n[ax] - 1 : q[ax] - 1;
-                const long long lo = wrap ? c + (long long)(n[ax] - 1) * s[ax] : c - s[ax];
-                off += A.W[ax][c] * (xin[lo] + parent(r[0], r[1], r[2]));
-            }
-            if (q[ax] < n[ax] - 1 || A.per[ax]) {
-                const bool wrap = q[ax] == n[ax] - 1;
-                r[ax] = wrap ? 0 : q[ax] + 1;
-                const long long hi = wrap ? c - (long long)(n[ax] - 1) * s[ax] : c + s[ax];
-                off += A.W[ax][hi] * (xin[hi] + parent(r[0], r[1], r[2]));
+__global__ void __launch_bounds__(COARSE_BLOCK) k_mg_coarse(const Op<T> A, const T* __restrict__ b,
+                                                            T* x, T* xt, T omega, int sweeps) {
+    T* buf[2] = {x, xt};
+    for (int s = 0; s < sweeps; ++s) {
+        const T* xin = buf[(s + 1) & 1];
+        T* xout = buf[s & 1];
+        for (long long c = threadIdx.x; c < A.N; c += COARSE_BLOCK) {
+            const T d = A.diag[c];
+            if (s == 0) {
+                xout[c] = omega * b[c] / d;
+            } else {
+                int i, j, k;
+                coords3(A, c, i, j, k);
+                const T xc = xin[c];
+                const T ax = apply_row(A, xin, c, i, j, k, xc);
+                xout[c] = xc + omega * (b[c] - ax) / d;
             }
         }
-        const T d = A.diag[c];
-        xout[c] = x0 + omega * (b[c] - (d * x0 - A.scale * off)) / d;
+        __syncthreads();
     }
 }
 
@@ -671,13 +656,9 @@ cudaError_t LinLaunch::smooth(const Op<T>& A, const T* b, const T* xin, T* xout,
     return end();
 }
 template <typename T>
-cudaError_t LinLaunch::smooth_prolong(const Op<T>& A, const T* b, const T* xin, const T* xc,
-                                      int cnx, int cny, T* xout, T omega) {
-    if (A.N == fine_N)
-        begin(sizeof(T) == 4 ? "mg_smooth_prolong_f32_fine" : "mg_smooth_prolong_f64_fine");
-    else begin(sizeof(T) == 4 ? "mg_smooth_prolong_f32" : "mg_smooth_prolong_f64");
-    k_mg_smooth_prolong<T><<<stream_blocks(A.N), LIN_BLOCK, 0, st>>>(A, b, xin, xc, cnx, cny,
-                                                                     xout, omega);
+cudaError_t LinLaunch::coarse_solve(const Op<T>& A, const T* b, T* x, T* xt, T omega, int sweeps) {
+    begin(sizeof(T) == 4 ? "mg_coarse_f32" : "mg_coarse_f64");
+    k_mg_coarse<T><<<1, COARSE_BLOCK, 0, st>>>(A, b, x, xt, omega, sweeps);
     return end();
 }
 template <typename T>
@@ -731,11 +712,10 @@ template cudaError_t LinLaunch::smooth<double>(const Op<double>&, const double*,
                                                double*, double, int);
 template cudaError_t LinLaunch::smooth<float>(const Op<float>&, const float*, const float*,
                                               float*, float, int);
-template cudaError_t LinLaunch::smooth_prolong<double>(const Op<double>&, const double*,
-                                                       const double*, const double*, int, int,
-                                                       double*, double);
-template cudaError_t LinLaunch::smooth_prolong<float>(const Op<float>&, const float*, const float*,
-                                                      const float*, int, int, float*, float);
+template cudaError_t LinLaunch::coarse_solve<double>(const Op<double>&, const double*, double*,
+                                                     double*, double, int);
+template cudaError_t LinLaunch::coarse_solve<float>(const Op<float>&, const float*, float*, float*,
+                                                    float, int);
 template cudaError_t LinLaunch::restrict_res<double>(const Op<double>&, const double*,
                                                      const double*, int, int, int, double*);
 template cudaError_t LinLaunch::restrict_res<float>(const Op<float>&, const float*, const float*,

@@ -30,6 +30,9 @@ struct OpNS {
     double scale;
 };
 
+// largest level solved by one single-CTA launch (all coarse sweeps)
+constexpr long long COARSE_MAX = 8192;
+
 // device scalar slots of the Krylov iterations
 enum { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RR, S_BREAK, S_TMP, S_RHO, S_OMEGA, S_SS, S_TS,
        S_TT, S_RV, S_NSCAL = 16 };
@@ -81,9 +84,10 @@ struct LinLaunch {
 
     template <typename T>
     cudaError_t smooth(const Op<T>& A, const T* b, const T* xin, T* xout, T omega, int first);
+    // every sweep of a level of at most COARSE_MAX cells in one single-CTA launch; the result
+    // ends in x when sweeps is odd, else in xt
     template <typename T>
-    cudaError_t smooth_prolong(const Op<T>& A, const T* b, const T* xin, const T* xc, int cnx,
-                               int cny, T* xout, T omega);
+    cudaError_t coarse_solve(const Op<T>& A, const T* b, T* x, T* xt, T omega, int sweeps);
     template <typename T>
     cudaError_t restrict_res(const Op<T>& A, const T* b, const T* x, int cnx, int cny, int cnz,
                              T* bc);
