@@ -93,8 +93,9 @@ def gaussian_random_field(shape, seed, slope=-2.0):
 
 def uniform_h(n=32, box=1.0 * MPC, nH=1e-3, T0=100.0, x0=1e-4, E0=1e-20, ndot=5e48,
               dt=1e12, nsteps=5, newton_tol=1e-8, lin_tol=1e-10, shape=None, name=None,
-              bc=("zero_flux",) * 6):
-    """Hydrogen-only uniform medium with a central source (the 32^3, 1 Mpc benchmark)."""
+              bc=("zero_flux",) * 6, source="centre"):
+    """Hydrogen-only uniform medium with a central source (the 32^3, 1 Mpc benchmark), or with
+    the source in the corner cell (0, 0, 0) (source = "corner", the HII-region test)."""
     nz, ny, nx = shape if shape is not None else (n, n, n)
     dx = box / nx
     nHf = np.full((nz, ny, nx), nH)
@@ -103,7 +104,10 @@ def uniform_h(n=32, box=1.0 * MPC, nH=1e-3, T0=100.0, x0=1e-4, E0=1e-20, ndot=5e
     z = np.zeros_like(nHf)
     e = _gas_energy(T0, nHf, z, nHII, z, z)
     # centre: the 8 cells around it for even sizes, the centre cell for odd sizes
-    cs = [[m // 2 - 1, m // 2] if m % 2 == 0 else [m // 2] for m in (nx, ny, nz)]
+    if source == "corner":
+        cs = [[0], [0], [0]]
+    else:
+        cs = [[m // 2 - 1, m // 2] if m % 2 == 0 else [m // 2] for m in (nx, ny, nz)]
     ijk = np.array([(i, j, k) for k in cs[2] for j in cs[1] for i in cs[0]])
     rate = np.full(len(ijk), ndot / len(ijk))
     return Workload(name=name or f"uniform_h_{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, dx=dx,
