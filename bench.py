@@ -44,13 +44,17 @@ def load_peaks():
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 
 # FP64 flops per cell of the fused cell kernels (bound by the FP64 pipe, about 1.2 TFLOP/s here),
-# counted by ncu as 2 DFMA + DMUL + DADD thread instructions per cell
+# counted by ncu as 2 DFMA + DMUL + DADD thread instructions per cell (177, 113, 78 on the
+# H + He lognormal 128^3 case)
 ALU_FLOPS = {
-    "cell_residual_schur": 585,
+    "cell_residual_schur": 545,
 }
-# DRAM bytes per launch (read + write) from ncu, scaled to the 256^3 workload; None once the
-# kernel has changed since the counters were taken
-TRAFFIC = {}
+# DRAM bytes per launch (read + write) from ncu, per cell of the 128^3 capture times the cells
+# of the timed grid (the kernel streams every field once, so traffic grows with the cells);
+# remove an entry when its kernel changes
+TRAFFIC_PER_CELL = {
+    "cell_residual_schur": 522.2e6 / 128 ** 3,
+}
 # launches bracketed by events inside the timed region
 # (the FP32 V-cycle replays as one CUDA graph, so its kernels are not bracketed one by one)
 TIMED_KERNELS = ["cell_residual_schur"]
@@ -444,13 +448,14 @@ def main():
         if tname in ALU_FLOPS:
             ach = ALU_FLOPS[tname] * w.N / avg_s / 1e12
             roof.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                        frac=ach / FP64_PEAK_TFLOPS, traffic=TRAFFIC.get(tname),
+                        frac=ach / FP64_PEAK_TFLOPS, traffic=TRAFFIC_PER_CELL[tname] * w.N if tname in TRAFFIC_PER_CELL else None,
                         flops_per_cell=ALU_FLOPS[tname],
                         peak_source="derived: 152 SMs x 2070 MHz x 2 DFMA/clk/SM x 2 flop")
         elif tname in ALG_BYTES:
             ach = ALG_BYTES[tname] * w.N / avg_s / 1e9
             roof.update(bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s",
-                        frac=ach / hbm_peak, traffic=TRAFFIC.get(tname),
+                        frac=ach / hbm_peak,
+                        traffic=TRAFFIC_PER_CELL[tname] * w.N if tname in TRAFFIC_PER_CELL else None,
                         peak_source=peak_src)
     # HBM fraction of the FP64 CG stencil / vector kernels (one full-grid launch each)
     lin = {}

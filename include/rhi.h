@@ -97,6 +97,9 @@ typedef struct {
     double mg_omega;        /* Jacobi weight                                                 */
     int vcycle_graph;       /* 1: the FP32 V-cycle is captured once as a CUDA graph and
                                replayed (on a library-owned stream ordered by events)       */
+    int dt_norm;            /* adaptive time steps (Sec. 3.2.3): 0 off; p >= 1 the p-norm and
+                               -1 the max norm of eq. time_error_estimator                  */
+    double dt_tau_tol;      /* tau_tol of eq. time_step_selection                            */
     /* grey constants per absorber (HI, HeI, HeII) of eq. adaptive_spectrum:
        kappa = sum sk_X n_X / a^3, Gamma_X = c pgam_X E / a^3, G = c E sum ph_X n_X / (a^3 rho) */
     double sk[3], pgam[3], ph[3];
@@ -119,6 +122,8 @@ typedef struct {
     double res_final;       /* ||f(U^{n+1})||                                                */
     double res_guess_prev;  /* ||f(U^n)|| when a learned guess was tried, else 0             */
     double ms;              /* device time of the last step, ms                              */
+    double eps_loc;         /* eq. time_error_estimator of the last step (dt_norm != 0)      */
+    double dt_next;         /* eq. time_step_selection: tau_tol dt / eps_loc (dt_norm != 0)  */
     double res_history[RHI_MAX_HISTORY];  /* ||f|| after 0, 1, .. Newton iterations      */
 } rhi_stats;
 
@@ -204,6 +209,17 @@ int rhi_precond_apply(rhi_handle h, const double* r, double* z, int on_device);
 int rhi_set_profiling(rhi_handle h, int on);
 int rhi_set_profiling_names(rhi_handle h, const char* names);
 int rhi_kernel_times(rhi_handle h, int max, char* names, double* total_ms, int* launches);
+
+/* Adaptive time stepping (Sec. 3.2.3; needs params.dt_norm != 0): implicit steps from the
+   current state until t_end, the first of length dt0, each later one the dt_next of its
+   predecessor, clamped to [dt_min, dt_max] and to the time left.  A step whose Newton
+   iteration fails is retried with half the step (the state is unchanged by a failed step),
+   down to dt_min.  Writes the time reached and the number of steps taken; returns RHI_OK, or
+   the error of a step that failed at dt_min, or RHI_ERR_NONCONVERGED after max_steps steps
+   short of t_end. */
+int rhi_advance(rhi_handle h, double t_end, double dt0, double dt_min, double dt_max, double a,
+                double adot, double newton_tol, double lin_tol, int max_steps, double* t_reached,
+                int* steps);
 
 /* Learned Newton initial guess (an addition; Sec. 3.2 leaves the initial iterate free): a
    per-cell MLP 9 -> 64 -> 64 -> 64 -> 6 with SiLU predicting the state at t^{n+1} from the

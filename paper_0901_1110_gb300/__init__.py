@@ -37,6 +37,7 @@ class rhi_params(C.Structure):
                 ("max_newton", C.c_int), ("max_pcg", C.c_int), ("guess", C.c_int),
                 ("precond", C.c_int), ("mg_levels", C.c_int), ("mg_pre", C.c_int),
                 ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double), ("vcycle_graph", C.c_int),
+                ("dt_norm", C.c_int), ("dt_tau_tol", C.c_double),
                 ("sk", C.c_double * 3), ("pgam", C.c_double * 3), ("ph", C.c_double * 3),
                 ("photon_energy", C.c_double)]
 
@@ -47,6 +48,7 @@ class rhi_stats(C.Structure):
                 ("guess_used", C.c_int), ("launches", C.c_int), ("guess_restarts", C.c_int),
                 ("res_initial", C.c_double),
                 ("res_final", C.c_double), ("res_guess_prev", C.c_double), ("ms", C.c_double),
+                ("eps_loc", C.c_double), ("dt_next", C.c_double),
                 ("res_history", C.c_double * 64)]
 
 
@@ -72,6 +74,9 @@ _SIGS = {
     "rhi_set_profiling_names": (C.c_int, [_P, C.c_char_p]),
     "rhi_kernel_times": (C.c_int, [_P, C.c_int, C.c_char_p, _D, C.POINTER(C.c_int)]),
     "rhi_rms_norm_noalloc": (C.c_int, [_P, C.c_longlong, C.c_longlong, _P, _P]),
+    "rhi_advance": (C.c_int, [_P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                              C.c_double, C.c_double, C.c_double, C.c_int, _D,
+                              C.POINTER(C.c_int)]),
     "rhi_mlp_set_weights": (C.c_int, [_P, _P, C.c_size_t]),
     "rhi_mlp_get_weights": (C.c_int, [_P, _P, C.c_size_t]),
     "rhi_mlp_features": (C.c_int, [_P, C.c_double, C.c_double, _P, C.c_int]),
@@ -226,6 +231,15 @@ class Solver:
     def step(self, dt, a=1.0, adot=0.0, newton_tol=1e-8, lin_tol=1e-10, check=True):
         return self._check(lib().rhi_implicit_step(self.h, dt, a, adot, newton_tol, lin_tol),
                            "rhi_implicit_step", check)
+
+    def advance(self, t_end, dt0, dt_min=0.0, dt_max=float("inf"), a=1.0, adot=0.0,
+                newton_tol=1e-8, lin_tol=1e-10, max_steps=100000):
+        """Adaptive steps (Sec. 3.2.3) until t_end; returns (time reached, steps taken)."""
+        t = C.c_double()
+        n = C.c_int()
+        self._check(lib().rhi_advance(self.h, t_end, dt0, dt_min, dt_max, a, adot, newton_tol,
+                                      lin_tol, max_steps, C.byref(t), C.byref(n)), "rhi_advance")
+        return t.value, n.value
 
     def get_state(self, E=None, e=None, n=None):
         """Host copies (numpy) unless device tensors are given to fill."""

@@ -108,6 +108,7 @@ struct rhi_ctx {
     double* W[2] = {nullptr, nullptr};
     double* PQ[2] = {nullptr, nullptr};         // Newton-matrix face entries (dD/dE kept)
     double* Kf[2] = {nullptr, nullptr};         // exact matrix: (1/2) dW/dkappa dE per face
+    double* Upred = nullptr;                    // explicit predictor of the step (dt_norm)
     double* diag_ns[2] = {nullptr, nullptr};
     double* g = nullptr;
     double *diag[2] = {nullptr, nullptr}, *rhs[2] = {nullptr, nullptr};
@@ -640,6 +641,7 @@ int validate_params(const rhi_params* p) {
     if (p->limiter_jacobian < 0 || p->limiter_jacobian > 2) return 0;
     if (!(p->mg_omega > 0.0 && p->mg_omega <= 1.0)) return 0;
     if (p->vcycle_graph != 0 && p->vcycle_graph != 1) return 0;
+    if (p->dt_norm < -1 || !(p->dt_tau_tol > 0.0)) return 0;
     return 1;
 }
 
@@ -747,6 +749,8 @@ int rhi_params_default(rhi_params* p, int n_species) {
     p->mg_coarse_sweeps = 16;
     p->mg_omega = 0.9;
     p->vcycle_graph = 1;
+    p->dt_norm = 0;
+    p->dt_tau_tol = 0.01;
     return rhi_grey_constants(RHI_SPECTRUM_MONO, 13.6 * EV, n_species, p->sk, p->pgam, p->ph,
                               &p->photon_energy);
 }
@@ -793,6 +797,7 @@ int rhi_create(const rhi_grid* grid, const rhi_bc* bc, const rhi_params* params,
         A(&h->rh, N); A(&h->v, N); A(&h->s, N); A(&h->t, N); A(&h->ph, N); A(&h->sh, N);
     }
     A(&h->g, (size_t)h->nv * N);
+    if (params->dt_norm) A(&h->Upred, (size_t)h->nv * N);
     A(&h->x, N); A(&h->r, N); A(&h->z, N); A(&h->p, N); A(&h->q, N);
     const long long nparts = std::max<long long>((N + cell_block_size() - 1) / cell_block_size(),
                                                  2 * (long long)stream_blocks(N));
@@ -1116,7 +1121,9 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
     S.guess_used = h->prm.guess;
     if (h->prm.guess == RHI_GUESS_PREVIOUS || h->prm.guess == RHI_GUESS_LEARNED) {
         B.diag = h->diag[0]; B.rhs = h->rhs[0]; B.fMt = h->fMt[0]; B.MiU = h->MiU[0];
+        B.U0 = h->Upred;                    // the explicit predictor, for the error estimate
         if ((rc = cell(h, P, MODE_PREP, B))) return rc;
+        B.U0 = nullptr;
         if ((rc = residual_norm(h, ncell_blocks(h), &res))) return rc;
         if (h->prm.guess == RHI_GUESS_LEARNED && h->mlp_skip > 0) {
             h->mlp_skip -= 1;
@@ -1152,6 +1159,9 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
     } else {
         B.U0 = h->U[0];
         if ((rc = cell(h, P, MODE_PREP_PREDICT, B))) return rc;
+        if (h->Upred)
+            CK(cudaMemcpyAsync(h->Upred, h->U[0], (size_t)h->nv * N * sizeof(double),
+                               cudaMemcpyDeviceToDevice, h->st));
         cur = 0;
         if ((rc = kappa(h, P, U_n(h, 0), h->kap[0]))) return rc;
         if ((rc = faces(h, P, U_E(h, 0), h->kap[0], 0))) return rc;
@@ -1270,6 +1280,22 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
         std::snprintf(buf, sizeof buf, "Newton: ||f|| = %.3e >= %.3e after %d iterations", res, newton_tol, k);
         return fail(h, RHI_ERR_NONCONVERGED, buf);
     }
+    // ---- error estimate against the explicit predictor (Sec. 3.2.3)
+    if (h->prm.dt_norm) {
+        const int nb = (int)std::min<long long>((N + 255) / 256, 152LL * 8);
+        const double pn = h->prm.dt_norm < 0 ? -1.0 : (double)h->prm.dt_norm;
+        {
+            Scope s(h->prof, "time_error");
+            CK(launch_time_error(P, ns, cur < 0 ? nullptr : U_ec(h, cur), cur < 0 ? h->n_s : U_n(h, cur),
+                                 cur < 0 ? h->E_s : U_E(h, cur), h->Upred, pn, h->partials, nb, h->st));
+        }
+        LinLaunch Le(h->st, &h->prof);
+        CK(Le.reduce(h->partials, nb, h->scal, pn < 0.0 ? RED_MAX : RED_SUM, S_TMP));
+        double v = 0.0;
+        if ((rc = read_scalar(h, S_TMP, &v))) return rc;
+        S.eps_loc = pn < 0.0 ? v : std::pow(v / ((double)N * h->nv), 1.0 / pn);
+        S.dt_next = S.eps_loc > 0.0 ? h->prm.dt_tau_tol * dt / S.eps_loc : HUGE_VAL;
+    }
     // ---- accept: U^{n+1} -> state, e^{n+1} = e_h + e_c
     if (cur >= 0) {
         {
@@ -1286,6 +1312,35 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
     S.ms = ms;
     S.launches = h->prof.launches - launches0;
     h->prof.resolve();
+    return RHI_OK;
+}
+
+int rhi_advance(rhi_handle h, double t_end, double dt0, double dt_min, double dt_max, double a,
+                double adot, double newton_tol, double lin_tol, int max_steps, double* t_reached,
+                int* steps) {
+    if (!h) return RHI_ERR_ARG;
+    if (!h->prm.dt_norm) return fail(h, RHI_ERR_ARG, "rhi_advance: params.dt_norm is 0");
+    if (!(t_end >= 0.0) || !(dt0 > 0.0) || !(dt_min >= 0.0) || !(dt_max >= dt_min) || max_steps < 0)
+        return fail(h, RHI_ERR_ARG, "rhi_advance: bad arguments");
+    double t = 0.0, dt = std::min(dt0, dt_max);
+    int n = 0, rc = RHI_OK;
+    while (t < t_end * (1.0 - 1e-12) && n < max_steps) {
+        double d = std::min(dt, t_end - t);
+        rc = rhi_implicit_step(h, d, a, adot, newton_tol, lin_tol);
+        while (rc == RHI_ERR_NONCONVERGED && 0.5 * d >= dt_min && 0.5 * d > 0.0) {
+            d *= 0.5;                           // the state is unchanged by a failed step
+            rc = rhi_implicit_step(h, d, a, adot, newton_tol, lin_tol);
+        }
+        if (rc) break;
+        t += d;
+        ++n;
+        dt = std::min(std::max(h->stats.dt_next, dt_min), dt_max);
+    }
+    if (t_reached) *t_reached = t;
+    if (steps) *steps = n;
+    if (rc) return rc;
+    if (t < t_end * (1.0 - 1e-12))
+        return fail(h, RHI_ERR_NONCONVERGED, "rhi_advance: max_steps reached before t_end");
     return RHI_OK;
 }
 

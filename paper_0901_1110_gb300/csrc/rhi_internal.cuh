@@ -176,5 +176,10 @@ cudaError_t launch_temperature(const StepParams& P, int ns, const double* e, con
 cudaError_t launch_check_state(const StepParams& P, int ns, const double* E, const double* e,
                                const double* n, const double* nH, int* bad, cudaStream_t st);
 cudaError_t launch_deposit(long long cell, double value, double* src, cudaStream_t st);
+// block partials (nblocks of 256 threads) of the step's error estimate against the predictor
+// Up: sum of q^pn, or max q when pn < 0
+cudaError_t launch_time_error(const StepParams& P, int ns, const double* ec, const double* n,
+                              const double* E, const double* Up, double pn, double* partials,
+                              int nblocks, cudaStream_t st);
 
 }  // namespace rhi

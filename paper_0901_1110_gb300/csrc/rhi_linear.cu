@@ -172,6 +172,20 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce(const double* __restrict__
                                                       int slot) {
     // the BiCGStab updates carry a second set of partials after the first n
     const bool two = op == RED_BICG_OMEGA || op == RED_BICG_RHO;
+    if (op == RED_MAX) {                        // max of non-negative partials
+        __shared__ double wmax[RED_BLOCK / 32];
+        double m = 0.0;
+        for (int q = threadIdx.x; q < n; q += RED_BLOCK) m = fmax(m, partials[q]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int q = 1; q < RED_BLOCK / 32; ++q) m = fmax(m, wmax[q]);
+            scal[slot] = fmax(m, wmax[0]);
+        }
+        return;
+    }
     double acc = 0.0, acc2 = 0.0;
     for (int q = threadIdx.x; q < n; q += RED_BLOCK) {
         acc += partials[q];

@@ -37,7 +37,7 @@ constexpr long long COARSE_MAX = 8192;
 enum { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RR, S_BREAK, S_TMP, S_RHO, S_OMEGA, S_SS, S_TS,
        S_TT, S_RV, S_NSCAL = 16 };
 enum { RED_SUM = 0, RED_ALPHA = 1, RED_BETA = 2, RED_BICG_ALPHA = 3, RED_BICG_OMEGA = 4,
-       RED_BICG_RHO = 5 };
+       RED_BICG_RHO = 5, RED_MAX = 6 };
 
 // number of blocks of the grid-stride streaming kernels (= number of partial sums)
 int stream_blocks(long long N);

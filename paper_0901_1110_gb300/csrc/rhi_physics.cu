@@ -472,8 +472,9 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const P
             for (int v = 0; v < NV; ++v) g[v] = B.g[v * N + c];
         }
 
-        if (MODE == MODE_PREP_PREDICT) {
-            // explicit Euler predictor U^n - dt L(U^n) (eq. explicit_predictor), positivity cap
+        if (MODE == MODE_PREP_PREDICT || (MODE == MODE_PREP && B.U0)) {
+            // explicit Euler predictor U^n - dt L(U^n) (eq. explicit_predictor), positivity cap;
+            // MODE_PREP writes it when the step estimates its error against it (Sec. 3.2.3)
             double d[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) d[v] = -P.dt * Lf[v];
@@ -493,7 +494,8 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const P
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) B.U0[v * N + c] = U[v] + cap * d[v];
-        } else {
+        }
+        if (MODE != MODE_PREP_PREDICT) {
             // scaled residual (eq. nonlinear_residual / eq. scalings)
             double fs[NV];
 #pragma unroll
@@ -692,6 +694,57 @@ __global__ void k_deposit(long long cell, double value, double* src) { src[cell]
 
 cudaError_t launch_deposit(long long cell, double value, double* src, cudaStream_t st) {
     k_deposit<<<1, 1, 0, st>>>(cell, value, src);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Local error estimate of the step against the explicit predictor (eqs. typical_values,
+// time_error_estimator): per scaled unknown q = |a - b| / (sqrt|a b| + 1); block partials of
+// sum q^p, or of max q when p < 0 (the max norm)
+
+template <int NS>
+__global__ void __launch_bounds__(256) k_time_error(const StepParams P, const double* __restrict__ ec,
+                                                    const double* __restrict__ n,
+                                                    const double* __restrict__ E,
+                                                    const double* __restrict__ Up, double pn,
+                                                    double* __restrict__ partials) {
+    constexpr int NV = NS + 2;
+    const long long N = P.N;
+    double acc = 0.0;
+    for (long long c = blockIdx.x * 256LL + threadIdx.x; c < N; c += (long long)gridDim.x * 256) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const double iu = v == 0 ? P.iu_e : (v == NV - 1 ? P.iu_E : P.iu_n);
+            const double a = (v == 0 ? (ec ? ec[c] : 0.0) : (v == NV - 1 ? E[c] : n[(v - 1) * N + c])) * iu;
+            const double b = Up[v * N + c] * iu;
+            const double q = fabs(a - b) / (sqrt(fabs(a * b)) + 1.0);
+            if (pn < 0.0) acc = fmax(acc, q);
+            else acc += (pn == 1.0) ? q : (pn == 2.0 ? q * q : pow(q, pn));
+        }
+    }
+    // block reduction (sum or max) in a fixed order
+    __shared__ double part[8];
+    if (pn < 0.0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc = fmax(acc, __shfl_down_sync(0xffffffffu, acc, o));
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    }
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = part[0];
+        for (int w = 1; w < 8; ++w) s = pn < 0.0 ? fmax(s, part[w]) : s + part[w];
+        partials[blockIdx.x] = s;
+    }
+}
+
+cudaError_t launch_time_error(const StepParams& P, int ns, const double* ec, const double* n,
+                              const double* E, const double* Up, double pn, double* partials,
+                              int nblocks, cudaStream_t st) {
+    if (ns == 1) k_time_error<1><<<nblocks, 256, 0, st>>>(P, ec, n, E, Up, pn, partials);
+    else k_time_error<3><<<nblocks, 256, 0, st>>>(P, ec, n, E, Up, pn, partials);
     return cudaGetLastError();
 }
 
