@@ -55,6 +55,7 @@ class Workload:
     u_E: float = 1.0
     bc: tuple = ("zero_flux",) * 6
     meta: dict = field(default_factory=dict)
+    schedule: list = None       # per step (dt, a, adot), cosmological runs
 
     @property
     def N(self):
@@ -120,8 +121,9 @@ def uniform_h(n=32, box=1.0 * MPC, nH=1e-3, T0=100.0, x0=1e-4, E0=1e-20, ndot=5e
 def lognormal_hhe(shape=(128, 128, 128), box=1.0 * MPC, seed=0, nbar=1e-3, sigma_ln=1.0,
                   nsrc=16, L50=1e49, Y=0.24, T0=100.0, x0=1e-4, E0=1e-20, T_B=1e5, dt=5e12,
                   nsteps=20, newton_tol=1e-8, lin_tol=1e-10, name=None,
-                  bc=("zero_flux",) * 6):
-    """Hydrogen + helium lognormal medium with seeded point sources (128^3 / 256^3 runs)."""
+                  bc=("zero_flux",) * 6, clustered=False):
+    """Hydrogen + helium lognormal medium with seeded point sources (128^3 / 256^3 runs);
+    clustered sources sit in cells drawn with probability proportional to n_H^2."""
     nz, ny, nx = shape
     dx = box / nx
     g = gaussian_random_field(shape, seed)
@@ -135,8 +137,14 @@ def lognormal_hhe(shape=(128, 128, 128), box=1.0 * MPC, seed=0, nbar=1e-3, sigma
     nHeI = nHe - nHeII - nHeIII
     e = _gas_energy(T0, nH, nHe, nHII, nHeII, nHeIII)
     rng = np.random.default_rng(seed + 7919)
-    ijk = np.stack([rng.integers(0, nx, nsrc), rng.integers(0, ny, nsrc),
-                    rng.integers(0, nz, nsrc)], axis=1)
+    if clustered:
+        w2 = (nH * nH).ravel()
+        flat = rng.choice(nH.size, size=nsrc, replace=False, p=w2 / w2.sum())
+        kk, jj, ii = np.unravel_index(flat, (nz, ny, nx))
+        ijk = np.stack([ii, jj, kk], axis=1)
+    else:
+        ijk = np.stack([rng.integers(0, nx, nsrc), rng.integers(0, ny, nsrc),
+                        rng.integers(0, nz, nsrc)], axis=1)
     rate = L50 * np.exp(rng.standard_normal(nsrc))
     return Workload(name=name or f"lognormal_hhe_{nx}x{ny}x{nz}_s{seed}", nx=nx, ny=ny, nz=nz,
                     dx=dx, ns=3, y_he=y_he, nH=nH, E=np.full_like(nH, E0), e=e,
@@ -169,3 +177,51 @@ def config_lognormal(n=128, nsrc=16, seed=0, box=1.0 * MPC):
     w.theta = 1.0
     w.u_E = U_E_SOURCES
     return w
+
+
+# flat Lambda-CDM expansion history (the cosmological configuration) -----------------------------
+
+H0_KMS_MPC = 70.0       # km/s/Mpc
+OMEGA_M = 0.3
+
+
+def _h0():
+    return H0_KMS_MPC * 1e5 / MPC                       # 1/s
+
+
+def flat_lcdm_a(t, omega_m=OMEGA_M):
+    """Scale factor of a flat matter + Lambda universe at cosmic time t (s):
+    a = (Om / OL)^(1/3) sinh(3/2 sqrt(OL) H0 t)^(2/3)."""
+    ol = 1.0 - omega_m
+    return (omega_m / ol) ** (1.0 / 3.0) * np.sinh(1.5 * np.sqrt(ol) * _h0() * np.asarray(t)) ** (2.0 / 3.0)
+
+
+def flat_lcdm_t(a, omega_m=OMEGA_M):
+    """Inverse of flat_lcdm_a."""
+    ol = 1.0 - omega_m
+    return np.arcsinh((np.asarray(a) / (omega_m / ol) ** (1.0 / 3.0)) ** 1.5) / (1.5 * np.sqrt(ol) * _h0())
+
+
+def flat_lcdm_adot(a, omega_m=OMEGA_M):
+    """da/dt = a H(a) = a H0 sqrt(Om a^-3 + OL)."""
+    a = np.asarray(a)
+    return a * _h0() * np.sqrt(omega_m / a ** 3 + (1.0 - omega_m))
+
+
+def config_cosmo(n=512, nsrc=256, seed=0, box=1.0 * MPC, z0=10.0, z1=6.0, nsteps=100):
+    """The cosmological configuration: H + He lognormal medium with sigma_ln = 1.5 (comoving
+    mean n_H = 1e-3), 256 lognormal sources in cells drawn with probability ~ n_H^2, theta = 1,
+    expansion from z = 10 to z = 6 in equal steps of cosmic time.  ``schedule`` holds (dt, a,
+    adot) of each step, a and adot taken at the middle of the step."""
+    w = lognormal_hhe((n, n, n), box=box, seed=seed, nsrc=nsrc, sigma_ln=1.5, clustered=True,
+                      nsteps=nsteps, name=f"cosmo_hhe_{n}", dt=1.0)
+    w.theta = 1.0
+    w.u_E = U_E_SOURCES
+    t0, t1 = flat_lcdm_t(1.0 / (1.0 + z0)), flat_lcdm_t(1.0 / (1.0 + z1))
+    dt = (t1 - t0) / nsteps
+    w.dt = float(dt)
+    mids = t0 + (np.arange(nsteps) + 0.5) * dt
+    a = flat_lcdm_a(mids)
+    w.schedule = [(float(dt), float(ai), float(flat_lcdm_adot(ai))) for ai in a]
+    return w
+
