@@ -190,6 +190,7 @@ StepParams make_params(const rhi_ctx* h, double dt, double a, double adot) {
     P.a = a; P.ia3 = 1.0 / (a * a * a); P.adot_a = adot / a;
     P.dt = dt; P.dth = dt * h->prm.theta; P.dtm1 = dt * (h->prm.theta - 1.0);
     P.inv_adx = 1.0 / (a * h->grid.dx);
+    P.half_adx = 0.5 * a * h->grid.dx;
     P.inv_a2dx2 = P.inv_adx * P.inv_adx;
     const int nmax = std::max(h->grid.nx, std::max(h->grid.ny, h->grid.nz));
     P.R_min = 1.0 / (a * nmax * h->grid.dx);

@@ -48,6 +48,7 @@ struct StepParams {
     double dt, dth, dtm1;             // dt, dt theta, dt (theta - 1)
     double inv_a2dx2;                 // 1 / (a dx)^2
     double inv_adx;                   // 1 / (a dx)
+    double half_adx;                  // a dx / 2
     double R_min;                     // limiter floor 1 / (a L)
     double kappa_floor;
     double m_grey;

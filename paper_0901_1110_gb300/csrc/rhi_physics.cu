@@ -63,7 +63,7 @@ __device__ __forceinline__ FaceCoef face_coef(const StepParams& P, double Ea, do
     r.K = 0.0;
     if (P.limiter) {
         const double Esum = Ea + Eb;
-        const double s = 0.5 * Esum / P.inv_adx;               // a dx Ebar
+        const double s = Esum * P.half_adx;                     // a dx Ebar
         const double dE = Eb - Ea;
         const double qraw = fabs(dE);
         const double q = fmax(qraw, P.R_min * s);
@@ -81,10 +81,12 @@ __device__ __forceinline__ FaceCoef face_coef(const StepParams& P, double Ea, do
             r.K = -0.5 * C_LIGHT * s * s * (12.0 * ks * ks + 12.0 * ks * q + q * q) * iden * iden *
                   P.inv_a2dx2 * dE;
         if (qraw > P.R_min * s) {
-            const double RdD = -C_LIGHT * q * q * (4.0 * ks + q) * s * iden * iden * P.inv_a2dx2;
-            const double t = dE / Esum;
-            r.P = r.W + RdD * (1.0 - t);
-            r.Q = r.W + RdD * (1.0 + t);
+            // R dD/dR (1 -+ t) with t = dE / Esum; s / Esum = a dx / 2, so RdD t needs no division
+            const double X = -C_LIGHT * q * q * (4.0 * ks + q) * iden * iden * P.inv_a2dx2;
+            const double RdD = X * s;
+            const double RdDt = X * dE * P.half_adx;
+            r.P = r.W + RdD - RdDt;
+            r.Q = r.W + RdD + RdDt;
         } else {
             r.P = r.Q = r.W;
         }
