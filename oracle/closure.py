@@ -33,6 +33,8 @@ M_H = 1.67262192e-24             # g, the proton mass m_p of eq. temperature
 EV = 1.602176634e-12             # erg
 H_PLANCK = 6.62607015e-27        # erg s
 GAMMA = 5.0 / 3.0                # ratio of specific heats (Sec. 2, below eq. eos)
+SIGMA_SB = 5.670374419e-5        # erg cm^-2 s^-1 K^-4, Stefan-Boltzmann constant (eq. LTE_coupling)
+A_RAD = 4.0 * SIGMA_SB / C_LIGHT # erg cm^-3 K^-4, radiation constant
 
 # ionisation thresholds (hnu_0 = 13.6 eV for hydrogen, Sec. 2.2)
 E_THR = np.array([13.6 * EV, 24.6 * EV, 54.4 * EV])        # HI, HeI, HeII

@@ -64,6 +64,12 @@ class Problem:
     growth_max: float = 1e3            # watchdog: a full step may raise ||f|| up to this factor
     watchdog: int = 3                  # ... for at most this many steps without a new best ||f||
     rates: object = field(default=None)
+    # LTE coupling (eq. LTE_coupling): no species (ns = 0), constant total and Planck-mean
+    # opacities, temperature from e with a fixed mean particle mass mu m_H
+    model: str = "ionization"          # "ionization" (non-LTE, Sec. 2.1) or "lte"
+    kappa_total: float = 0.0           # cm^-1
+    kappa_planck: float = 0.0          # cm^-1
+    mu: float = 0.6
 
     def __post_init__(self):
         if self.rates is None:
@@ -72,6 +78,8 @@ class Problem:
         self.src = np.ascontiguousarray(self.src, dtype=np.float64).ravel()
         if self.ns == 1 and self.y_he != 0.0:
             raise ValueError("hydrogen-only runs have y_he = 0")
+        if (self.model == "lte") != (self.ns == 0):
+            raise ValueError("the LTE model has no species (ns = 0), the ionization model 1 or 3")
         for lo, hi in ((0, 1), (2, 3), (4, 5)):
             if (self.bc[lo] == BC_PERIODIC) != (self.bc[hi] == BC_PERIODIC):
                 raise ValueError("periodic boundaries come in pairs")
@@ -131,6 +139,8 @@ def local_terms(p, ec, n, E, eh, nH, src, a, adot, T_fixed=None, want_jac=False)
       dLx[a][b]  d(local operator a) / d(unknown b), a, b over (e_c, n_1, ..)
       dLxE[a]    d(local operator a) / dE
       dLEx[b]    d LE / d(unknown b);   dLEE  d LE / dE""" 
+    if p.model == "lte":
+        return _local_terms_lte(p, ec, E, eh, nH, src, a, adot, T_fixed, want_jac)
     ns = p.ns
     c = cl.C_LIGHT
     ia3 = 1.0 / a ** 3
@@ -229,6 +239,44 @@ def local_terms(p, ec, n, E, eh, nH, src, a, adot, T_fixed=None, want_jac=False)
         dLxE[1 + s] = dAdE[s]
     dLEx = [np.zeros_like(e)] + [c * ia3 * sk[j] * E for j in range(ns)]
     dLEE = p.m_grey * adot / a + c * kap
+    out.update(dLx=dLx, dLxE=dLxE, dLEx=dLEx, dLEE=dLEE)
+    return out
+
+
+def _local_terms_lte(p, ec, E, eh, nH, src, a, adot, T_fixed, want_jac):
+    """Local operators of the LTE model (eq. LTE_coupling): emission 4 pi eta = 4 kappa_P
+    sigma_SB T^4, heating G = c kappa E / rho and cooling Lambda = 4 pi eta / rho, with
+    T = (gamma - 1) mu m_H e / k_B.  L_e = 2 (adot/a) e_c - G + Lambda (eq. mLe with these
+    terms) and the local part of L_E = m (adot/a) E - 4 pi eta_src + c kappa E - 4 pi eta
+    (eq. mLE).  The opacities are used as given (no 1/a^3 factor)."""
+    c = cl.C_LIGHT
+    e = eh + ec
+    rho = cl.M_H * nH * (1.0 + 4.0 * p.y_he)
+    cT = (cl.GAMMA - 1.0) * p.mu * cl.M_H / cl.K_BOLTZ      # T = cT e
+    if p.isothermal:
+        T = T_fixed
+        dT_dec = np.zeros_like(e)
+    else:
+        T = cT * e
+        dT_dec = np.full_like(e, cT)
+    kap = np.full_like(e, p.kappa_total)
+    emis = 4.0 * p.kappa_planck * cl.SIGMA_SB * T ** 4                # 4 pi eta_LTE
+    G = c * p.kappa_total * E / rho
+    Lam = emis / rho
+    Le = np.zeros_like(e) if p.isothermal else 2.0 * (adot / a) * ec - G + Lam
+    LE = p.m_grey * (adot / a) * E - src + c * p.kappa_total * E - emis
+    out = dict(L=[Le], LE=LE, kappa=kap, T=T, ne=np.zeros_like(e), rho=rho)
+    if not want_jac:
+        return out
+    demis = 16.0 * p.kappa_planck * cl.SIGMA_SB * T ** 3 * dT_dec     # d(4 pi eta)/d e_c
+    if p.isothermal:
+        dLx = [[np.zeros_like(e)]]
+        dLxE = [np.zeros_like(e)]
+    else:
+        dLx = [[2.0 * adot / a + demis / rho]]
+        dLxE = [-c * p.kappa_total / rho]
+    dLEx = [-demis]
+    dLEE = p.m_grey * adot / a + c * p.kappa_total + 0.0 * e
     out.update(dLx=dLx, dLxE=dLxE, dLEx=dLEx, dLEE=dLEE)
     return out
 
@@ -364,6 +412,8 @@ def state_to_U(p, state):
 def fixed_temperature(p, state):
     """Temperature of each cell of a state (e, n); isothermal runs hold it fixed."""
     eh = np.asarray(state["e"]).ravel()
+    if p.model == "lte":
+        return (cl.GAMMA - 1.0) * p.mu * cl.M_H / cl.K_BOLTZ * eh
     n = np.asarray(state["n"]).reshape(p.ns, p.N)
     nHI, nHeI, nHeII = p.species_full(n)
     nHe = p.y_he * p.nH

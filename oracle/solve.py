@@ -50,6 +50,8 @@ def _cell_quantities(p, U, eh):
     each with its roundoff allowance below zero: 0 for e and E, 1e-13 of the element total for
     the species."""
     ns = p.ns
+    if ns == 0:                                    # LTE: gas and radiation energy only
+        return [(eh + U[0], 0.0), (U[1], 0.0)]
     nHI, nHeI, nHeII = p.species_full(U[1:1 + ns])
     nHe = p.y_he * p.nH
     nHII, nHeIII, _ = cl.derived_species(p.nH, nHe, nHI, nHeI, nHeII)
@@ -61,6 +63,8 @@ def _cell_quantities(p, U, eh):
 
 def _quantity_changes(p, S):
     ns = p.ns
+    if ns == 0:
+        return [S[0], S[1]]
     dHI = S[1]
     out = [S[0], S[1 + ns], dHI, -dHI]
     if ns == 3:

@@ -56,6 +56,10 @@ class Workload:
     bc: tuple = ("zero_flux",) * 6
     meta: dict = field(default_factory=dict)
     schedule: list = None       # per step (dt, a, adot), cosmological runs
+    model: str = "ionization"   # "ionization" (species) or "lte" (ns = 0, constant opacities)
+    kappa_total: float = 0.0    # cm^-1 (LTE)
+    kappa_planck: float = 0.0   # cm^-1 (LTE)
+    mu: float = 0.6             # mean particle mass / m_H (LTE temperature)
 
     @property
     def N(self):
@@ -64,7 +68,7 @@ class Workload:
     def state(self):
         """Flat copies (x fastest) of the initial state: dict(E, e, n)."""
         return dict(E=self.E.ravel().copy(), e=self.e.ravel().copy(),
-                    n=self.n.reshape(self.ns, -1).copy())
+                    n=self.n.reshape(self.ns, self.N).copy())
 
 
 def _gas_energy(T0, nH, nHe, nHII, nHeII, nHeIII):
@@ -224,4 +228,23 @@ def config_cosmo(n=512, nsrc=256, seed=0, box=1.0 * MPC, z0=10.0, z1=6.0, nsteps
     a = flat_lcdm_a(mids)
     w.schedule = [(float(dt), float(ai), float(flat_lcdm_adot(ai))) for ai in a]
     return w
+
+
+# LTE coupling: matter-radiation equilibration (the Turner-Stone set-up) ---------------------------
+
+def lte_uniform(e_vol, n=4, rho=1e-7, E0=1e12, kappa=4e-8, mu=0.6, box=1.0, dt=1e-12, nsteps=50,
+                bc=("periodic",) * 6, E_perturb=0.0, seed=0):
+    """A box of uniform LTE gas (eq. LTE_coupling) with gas energy density e_vol (erg cm^-3),
+    density rho, radiation energy density E0 and one opacity for both means; E_perturb adds a
+    seeded relative perturbation to E so that diffusion takes part.  Box in cm."""
+    nH = np.full((n, n, n), rho / _MH)
+    e = np.full_like(nH, e_vol / rho)
+    E = np.full_like(nH, E0)
+    if E_perturb:
+        E = E * (1.0 + E_perturb * np.random.default_rng(seed).standard_normal(E.shape))
+    return Workload(name=f"lte_{n}", nx=n, ny=n, nz=n, dx=box / n, ns=0, y_he=0.0, nH=nH,
+                    E=E, e=e, n=np.zeros((0, n, n, n)), src_ijk=np.zeros((0, 3), dtype=np.int64),
+                    src_rate=np.zeros(0), spectrum=("mono", 13.6 * _EV), dt=dt, nsteps=nsteps,
+                    theta=1.0, u_e=float(e.mean()), u_n=1.0, u_E=float(E0), bc=tuple(bc),
+                    model="lte", kappa_total=kappa, kappa_planck=kappa, mu=mu)
 
