@@ -45,6 +45,10 @@ extern "C" {
 
 enum { RHI_BC_ZERO_FLUX = 0, RHI_BC_PERIODIC = 1 };
 enum { RHI_GUESS_PREVIOUS = 0, RHI_GUESS_PREDICTOR = 1, RHI_GUESS_LEARNED = 2 };
+/* physics model: non-LTE ionization chemistry (Sec. 2.1, n_species 1 or 3), or the LTE
+   coupling of eq. LTE_coupling (n_species 0: gas and radiation energy only, constant total
+   and Planck-mean opacities, T = (gamma - 1) mu m_H e / k_B) */
+enum { RHI_MODEL_IONIZATION = 0, RHI_MODEL_LTE = 1 };
 enum { RHI_PRECOND_JACOBI = 0, RHI_PRECOND_MG_FP64 = 1, RHI_PRECOND_MG_FP32 = 2 };
 enum { RHI_SPECTRUM_MONO = 0, RHI_SPECTRUM_BLACKBODY = 1, RHI_SPECTRUM_POWERLAW = 2 };
 
@@ -61,7 +65,7 @@ typedef struct {
 
 /* Method and closure parameters.  Fill with rhi_params_default, then override. */
 typedef struct {
-    int n_species;          /* 1: H (HI); 3: H + He (HI, HeI, HeII)                          */
+    int n_species;          /* 1: H (HI); 3: H + He (HI, HeI, HeII); 0: the LTE model       */
     double y_he;            /* n_He / n_H; 0 when n_species = 1                              */
     double theta;           /* theta of the two-level scheme (Sec. 3.2)                      */
     int m_grey;             /* m of eq. cons_radiation (1 grey, 0 monochromatic)             */
@@ -100,6 +104,10 @@ typedef struct {
     int dt_norm;            /* adaptive time steps (Sec. 3.2.3): 0 off; p >= 1 the p-norm and
                                -1 the max norm of eq. time_error_estimator                  */
     double dt_tau_tol;      /* tau_tol of eq. time_step_selection                            */
+    int model;              /* RHI_MODEL_* (rhi_params_default(0) selects the LTE model)     */
+    double kappa_total;     /* LTE: total opacity, cm^-1 (absorption and the limiter)        */
+    double kappa_planck;    /* LTE: Planck-mean opacity, cm^-1 (emission)                    */
+    double mu;              /* LTE: mean particle mass in units of m_H                       */
     /* grey constants per absorber (HI, HeI, HeII) of eq. adaptive_spectrum:
        kappa = sum sk_X n_X / a^3, Gamma_X = c pgam_X E / a^3, G = c E sum ph_X n_X / (a^3 rho) */
     double sk[3], pgam[3], ph[3];

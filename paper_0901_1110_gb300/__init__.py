@@ -18,6 +18,7 @@ RHI_BC_ZERO_FLUX, RHI_BC_PERIODIC = 0, 1
 RHI_GUESS_PREVIOUS, RHI_GUESS_PREDICTOR, RHI_GUESS_LEARNED = 0, 1, 2
 RHI_PRECOND_JACOBI, RHI_PRECOND_MG_FP64, RHI_PRECOND_MG_FP32 = 0, 1, 2
 RHI_SPECTRUM_MONO, RHI_SPECTRUM_BLACKBODY, RHI_SPECTRUM_POWERLAW = 0, 1, 2
+RHI_MODEL_IONIZATION, RHI_MODEL_LTE = 0, 1
 
 
 class rhi_grid(C.Structure):
@@ -37,7 +38,8 @@ class rhi_params(C.Structure):
                 ("max_newton", C.c_int), ("max_pcg", C.c_int), ("guess", C.c_int),
                 ("precond", C.c_int), ("mg_levels", C.c_int), ("mg_pre", C.c_int),
                 ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double), ("vcycle_graph", C.c_int),
-                ("dt_norm", C.c_int), ("dt_tau_tol", C.c_double),
+                ("dt_norm", C.c_int), ("dt_tau_tol", C.c_double), ("model", C.c_int),
+                ("kappa_total", C.c_double), ("kappa_planck", C.c_double), ("mu", C.c_double),
                 ("sk", C.c_double * 3), ("pgam", C.c_double * 3), ("ph", C.c_double * 3),
                 ("photon_energy", C.c_double)]
 
@@ -216,7 +218,7 @@ class Solver:
     def set_state(self, E, e, n, nH, src=None):
         (pE, d0), (pe, d1), (pn, d2), (pH, d3) = _ptr(E), _ptr(e), _ptr(n), _ptr(nH)
         ps, d4 = _ptr(src)
-        devs = {d0, d1, d2, d3} | ({d4} if src is not None else set())
+        devs = {d0, d1, d3} | ({d2} if n is not None else set()) | ({d4} if src is not None else set())
         if len(devs) != 1:
             raise TypeError("all fields on the host or all on the device")
         return self._check(lib().rhi_set_state(self.h, pE, pe, pn, pH, ps, d0), "rhi_set_state")
@@ -383,6 +385,9 @@ def params_for_workload(w, **overrides):
     grey constants the library computes for the workload's spectrum."""
     p = rhi_params_default(w.ns)
     p.y_he = w.y_he
+    if w.model == "lte":
+        p.model = RHI_MODEL_LTE
+        p.kappa_total, p.kappa_planck, p.mu = w.kappa_total, w.kappa_planck, w.mu
     p.theta = w.theta
     p.u_e, p.u_n, p.u_E = w.u_e, w.u_n, w.u_E
     kind, par = w.spectrum
@@ -407,7 +412,7 @@ def solver_for_workload(w, stream=None, sources=True, **overrides):
     bc = [RHI_BC_PERIODIC if b == "periodic" else RHI_BC_ZERO_FLUX for b in w.bc]
     s = Solver(w.nx, w.ny, w.nz, w.dx, p, bc=bc, stream=stream)
     st = w.state()
-    s.set_state(st["E"], st["e"], np.ascontiguousarray(st["n"]).ravel(),
+    s.set_state(st["E"], st["e"], np.ascontiguousarray(st["n"]).ravel() if w.ns else None,
                 np.ascontiguousarray(w.nH.ravel()))
     if sources and len(w.src_rate):
         s.set_sources(w.src_ijk, w.src_rate)

@@ -121,7 +121,7 @@ double bose_inverse(double y0) {
 extern "C" int rhi_grey_constants(int spectrum, double param, int n_species, double* sk,
                                   double* pgam, double* ph, double* photon_energy) {
     if (!sk || !pgam || !ph || !photon_energy) return RHI_ERR_ARG;
-    if (n_species != 1 && n_species != 3) return RHI_ERR_ARG;
+    if (n_species != 0 && n_species != 1 && n_species != 3) return RHI_ERR_ARG;
     for (int X = 0; X < 3; ++X) sk[X] = pgam[X] = ph[X] = 0.0;
     if (spectrum == RHI_SPECTRUM_MONO) {
         const double hnu = param;

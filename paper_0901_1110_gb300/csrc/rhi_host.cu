@@ -209,6 +209,10 @@ StepParams make_params(const rhi_ctx* h, double dt, double a, double adot) {
     P.sc_nE = P.dth * P.u_n * P.iu_E;
     for (int X = 0; X < 3; ++X) { P.sk[X] = h->prm.sk[X]; P.pg[X] = h->prm.pgam[X]; P.ph[X] = h->prm.ph[X]; }
     P.tau = h->prm.tau;
+    P.lte = h->prm.model == RHI_MODEL_LTE;
+    P.kappa_total = h->prm.kappa_total;
+    P.kappa_planck = h->prm.kappa_planck;
+    P.lte_cT = (GAMMA - 1.0) * h->prm.mu * M_H / K_BOLTZ;
     P.table = h->table;
     return P;
 }
@@ -625,8 +629,13 @@ double* U_n(rhi_ctx* h, int b) { return h->U[b] + h->N; }
 double* U_E(rhi_ctx* h, int b) { return h->U[b] + (long long)(1 + h->ns) * h->N; }
 
 int validate_params(const rhi_params* p) {
-    if (p->n_species != 1 && p->n_species != 3) return 0;
+    if (p->n_species != 0 && p->n_species != 1 && p->n_species != 3) return 0;
     if (p->n_species == 1 && p->y_he != 0.0) return 0;
+    if ((p->model == RHI_MODEL_LTE) != (p->n_species == 0)) return 0;
+    if (p->model == RHI_MODEL_LTE &&
+        (!(p->kappa_total >= 0.0) || !(p->kappa_planck >= 0.0) || !(p->mu > 0.0) ||
+         p->guess == RHI_GUESS_LEARNED))
+        return 0;
     if (!(p->y_he >= 0.0)) return 0;
     if (!(p->theta > 0.0 && p->theta <= 1.0)) return 0;
     if (!(p->u_e > 0.0 && p->u_n > 0.0 && p->u_E > 0.0)) return 0;
@@ -721,7 +730,7 @@ int mlp_grad(rhi_ctx* h, const float* X, const float* Y, long long m, double* pa
 extern "C" {
 
 int rhi_params_default(rhi_params* p, int n_species) {
-    if (!p || (n_species != 1 && n_species != 3)) return RHI_ERR_ARG;
+    if (!p || (n_species != 0 && n_species != 1 && n_species != 3)) return RHI_ERR_ARG;
     std::memset(p, 0, sizeof(*p));
     p->n_species = n_species;
     p->y_he = 0.0;
@@ -752,6 +761,10 @@ int rhi_params_default(rhi_params* p, int n_species) {
     p->vcycle_graph = 1;
     p->dt_norm = 0;
     p->dt_tau_tol = 0.01;
+    p->model = n_species == 0 ? RHI_MODEL_LTE : RHI_MODEL_IONIZATION;
+    p->kappa_total = 0.0;
+    p->kappa_planck = 0.0;
+    p->mu = 0.6;
     return rhi_grey_constants(RHI_SPECTRUM_MONO, 13.6 * EV, n_species, p->sk, p->pgam, p->ph,
                               &p->photon_energy);
 }
@@ -862,12 +875,12 @@ const char* rhi_status_string(int s) {
 int rhi_set_state(rhi_handle h, const double* E, const double* e, const double* n,
                   const double* n_H, const double* src, int on_device) {
     if (!h) return RHI_ERR_ARG;
-    if (!E || !e || !n || !n_H) return fail(h, RHI_ERR_ARG, "rhi_set_state: null field");
+    if (!E || !e || (!n && h->ns > 0) || !n_H) return fail(h, RHI_ERR_ARG, "rhi_set_state: null field");
     const long long N = h->N;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CK(cudaMemcpyAsync(h->E_s, E, N * sizeof(double), kind, h->st));
     CK(cudaMemcpyAsync(h->e_s, e, N * sizeof(double), kind, h->st));
-    CK(cudaMemcpyAsync(h->n_s, n, (size_t)h->ns * N * sizeof(double), kind, h->st));
+    if (h->ns > 0) CK(cudaMemcpyAsync(h->n_s, n, (size_t)h->ns * N * sizeof(double), kind, h->st));
     CK(cudaMemcpyAsync(h->nH, n_H, N * sizeof(double), kind, h->st));
     if (src) CK(cudaMemcpyAsync(h->src, src, N * sizeof(double), kind, h->st));
     else CK(cudaMemsetAsync(h->src, 0, N * sizeof(double), h->st));
@@ -1058,6 +1071,7 @@ int rhi_residual(rhi_handle h, double dt, double a, double adot, const double* U
 
 int rhi_mlp_guess(rhi_handle h, double dt, double a, double* U0, int on_device) {
     if (!h) return RHI_ERR_ARG;
+    if (h->ns == 0) return fail(h, RHI_ERR_ARG, "rhi_mlp_guess: the learned guess needs the ionization model");
     if (!h->have_state) return fail(h, RHI_ERR_STATE, "rhi_mlp_guess: no state");
     if (!h->mlp_ready) return fail(h, RHI_ERR_STATE, "rhi_mlp_guess: no weights set");
     if (!U0 || !(dt > 0.0) || !(a > 0.0)) return fail(h, RHI_ERR_ARG, "rhi_mlp_guess: bad arguments");
@@ -1387,6 +1401,7 @@ int rhi_mlp_get_weights(rhi_handle h, float* w, size_t n) {
 
 int rhi_mlp_features(rhi_handle h, double dt, double a, float* X, int on_device) {
     if (!h) return RHI_ERR_ARG;
+    if (h->ns == 0) return fail(h, RHI_ERR_ARG, "rhi_mlp_features: the learned guess needs the ionization model");
     if (!h->have_state) return fail(h, RHI_ERR_STATE, "rhi_mlp_features: no state");
     if (!X || !(dt > 0.0) || !(a > 0.0)) return fail(h, RHI_ERR_ARG, "rhi_mlp_features: bad arguments");
     const MlpArgs A = mlp_args(h, dt, a);
@@ -1407,6 +1422,7 @@ int rhi_mlp_features(rhi_handle h, double dt, double a, float* X, int on_device)
 int rhi_mlp_targets(rhi_handle h, const double* E_old, const double* e_old, const double* n_old,
                     float* Y, int on_device) {
     if (!h) return RHI_ERR_ARG;
+    if (h->ns == 0) return fail(h, RHI_ERR_ARG, "rhi_mlp_targets: the learned guess needs the ionization model");
     if (!h->have_state) return fail(h, RHI_ERR_STATE, "rhi_mlp_targets: no state");
     if (!E_old || !e_old || !n_old || !Y) return fail(h, RHI_ERR_ARG, "rhi_mlp_targets: null argument");
     const long long N = h->N;

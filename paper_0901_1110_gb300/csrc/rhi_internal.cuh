@@ -19,6 +19,7 @@ constexpr double K_BOLTZ = 1.380649e-16;
 constexpr double M_H = 1.67262192e-24;    // proton mass
 constexpr double EV = 1.602176634e-12;
 constexpr double GAMMA = 5.0 / 3.0;
+constexpr double SIGMA_SB = 5.670374419e-5;   // erg cm^-2 s^-1 K^-4
 
 // rate table: 2^TABLE_BITS bins per octave of T over [2^0, 2^TABLE_OCTAVES) K
 constexpr int TABLE_BITS = 6;
@@ -61,6 +62,9 @@ struct StepParams {
     double sc_ne, sc_en, sc_Ee, sc_En, sc_eE, sc_nE;
     double sk[3], pg[3], ph[3];
     double tau;
+    // LTE coupling (eq. LTE_coupling; no species): constant opacities, T = lte_cT e
+    int lte;
+    double kappa_total, kappa_planck, lte_cT;
     const double2* __restrict__ table;
 };
 

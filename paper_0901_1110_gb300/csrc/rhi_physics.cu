@@ -21,6 +21,7 @@ __global__ void k_kappa(const StepParams P, int ns, const double* __restrict__ n
                         double* __restrict__ kap) {
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= P.N) return;
+    if (ns == 0) { kap[c] = P.kappa_total; return; }          // LTE: constant opacity
     double s = P.sk[0] * n[c];
     if (ns == 3) s += P.sk[1] * n[P.N + c] + P.sk[2] * n[2 * P.N + c];
     kap[c] = P.ia3 * s;
@@ -196,6 +197,7 @@ cudaError_t launch_schur_kappa(const StepParams& P, int ns, const double* K, con
                                cudaStream_t st) {
     const int b = 256;
     const unsigned g = (unsigned)((P.N + b - 1) / b);
+    if (ns == 0) return cudaSuccess;                  // constant opacity: no coupling
     if (ns == 1) k_schur_kappa<1><<<g, b, 0, st>>>(P, K, fMt, MiU, PQ, diag_ns, rhs);
     else k_schur_kappa<3><<<g, b, 0, st>>>(P, K, fMt, MiU, PQ, diag_ns, rhs);
     return cudaGetLastError();
@@ -242,9 +244,29 @@ struct Local {
 };
 
 template <int NS, bool JAC>
-__device__ __forceinline__ void local_model(const StepParams& P, double ec, const double (&n)[NS],
+__device__ __forceinline__ void local_model(const StepParams& P, double ec,
+                                            const double (&n)[NS > 0 ? NS : 1],
                                             double E, double eh, double nH, double src,
                                             double Tfix, Local<NS>& o) {
+    if constexpr (NS == 0) {
+        // LTE coupling (eq. LTE_coupling): emission 4 pi eta = 4 kappa_P sigma T^4, heating
+        // c kappa E / rho, cooling 4 pi eta / rho; T = lte_cT e
+        const double rho = M_H * nH * (1.0 + 4.0 * P.y_he), irho = 1.0 / rho;
+        const double e = eh + ec;
+        const double T = P.isothermal ? Tfix : P.lte_cT * e;
+        const double T2 = T * T;
+        const double emis = 4.0 * P.kappa_planck * SIGMA_SB * T2 * T2;
+        const double ckE = C_LIGHT * P.kappa_total * E;
+        o.L[0] = P.isothermal ? 0.0 : (2.0 * P.adot_a * ec - ckE * irho + emis * irho);
+        o.LE = P.m_grey * P.adot_a * E - src + ckE - emis;
+        if constexpr (!JAC) return;
+        const double demis = P.isothermal ? 0.0 : 16.0 * P.kappa_planck * SIGMA_SB * T2 * T * P.lte_cT;
+        o.dLx[0][0] = P.isothermal ? 0.0 : 2.0 * P.adot_a + demis * irho;
+        o.dLxE[0] = P.isothermal ? 0.0 : -C_LIGHT * P.kappa_total * irho;
+        o.dLEx[0] = -demis;
+        o.dLEE = P.m_grey * P.adot_a + C_LIGHT * P.kappa_total;
+        return;
+    } else {
     const double c = C_LIGHT, ia3 = P.ia3;
     const double nHe = P.y_he * nH;
     const double nHI = n[0];
@@ -363,6 +385,7 @@ __device__ __forceinline__ void local_model(const StepParams& P, double ec, cons
 #pragma unroll
     for (int j = 0; j < NS; ++j) o.dLEx[1 + j] = c * ia3 * P.sk[j] * E;
     o.dLEE = P.m_grey * P.adot_a + c * kap;
+    }
 }
 
 // Gaussian elimination with partial pivoting for two right-hand sides (step (i), eq. step_ia)
@@ -429,7 +452,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const P
         const double* En = prep ? B.E_n : B.E;
         const double* nn = prep ? B.n_n : B.n;
         const double E = En[c];
-        double n[NS];
+        double n[NS > 0 ? NS : 1];
 #pragma unroll
         for (int s = 0; s < NS; ++s) n[s] = nn[s * N + c];
         const double ec = (prep || B.ec == nullptr) ? 0.0 : B.ec[c];
@@ -486,8 +509,10 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const P
             };
             bound(eh + ec, d[0], 0.0);
             bound(E, d[NV - 1], 0.0);
-            bound(n[0], d[1], 1e-13 * nH);
-            bound(nH - n[0], -d[1], 1e-13 * nH);
+            if constexpr (NS >= 1) {
+                bound(n[0], d[1], 1e-13 * nH);
+                bound(nH - n[0], -d[1], 1e-13 * nH);
+            }
             if constexpr (NS == 3) {
                 const double nHe = P.y_he * nH;
                 bound(n[1], d[2], 1e-13 * nHe);
@@ -544,7 +569,11 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const P
 cudaError_t launch_cell(const StepParams& P, int ns, int mode, const PhysBuffers& B,
                         int nblocks, cudaStream_t st) {
     const dim3 g(nblocks), b(CELL_BLOCK);
-    if (ns == 1) {
+    if (ns == 0) {
+        if (mode == MODE_PREP) k_cell<0, MODE_PREP><<<g, b, 0, st>>>(P, B);
+        else if (mode == MODE_ITER) k_cell<0, MODE_ITER><<<g, b, 0, st>>>(P, B);
+        else k_cell<0, MODE_PREP_PREDICT><<<g, b, 0, st>>>(P, B);
+    } else if (ns == 1) {
         if (mode == MODE_PREP) k_cell<1, MODE_PREP><<<g, b, 0, st>>>(P, B);
         else if (mode == MODE_ITER) k_cell<1, MODE_ITER><<<g, b, 0, st>>>(P, B);
         else k_cell<1, MODE_PREP_PREDICT><<<g, b, 0, st>>>(P, B);
@@ -584,7 +613,7 @@ __global__ void __launch_bounds__(256) k_update(const StepParams P, double lam,
     for (int r = 0; r < NM; ++r) s[r] = (-fMt[r * N + c] - MiU[r * N + c] * se) * (r == 0 ? P.u_e : P.u_n);
     const double sEp = se * P.u_E;
     const double ec = ec0 ? ec0[c] : 0.0;
-    double n[NS];
+    double n[NS > 0 ? NS : 1];
 #pragma unroll
     for (int j = 0; j < NS; ++j) n[j] = n0[j * N + c];
     const double E = E0[c], nH = nHa[c];
@@ -599,8 +628,10 @@ __global__ void __launch_bounds__(256) k_update(const StepParams P, double lam,
     };
     bound(eh[c] + ec, s[0], 0.0);
     bound(E, sEp, 0.0);
-    bound(n[0], s[1], 1e-13 * nH);
-    bound(nH - n[0], -s[1], 1e-13 * nH);
+    if constexpr (NS >= 1) {
+        bound(n[0], s[1], 1e-13 * nH);
+        bound(nH - n[0], -s[1], 1e-13 * nH);
+    }
     if constexpr (NS == 3) {
         const double nHe = P.y_he * nH;
         bound(n[1], s[2], 1e-13 * nHe);
@@ -618,7 +649,7 @@ __global__ void __launch_bounds__(256) k_update(const StepParams P, double lam,
         ksum += P.sk[j] * v;
     }
     E1[c] = E + fr * sEp;
-    kap1[c] = P.ia3 * ksum;
+    kap1[c] = NS == 0 ? P.kappa_total : P.ia3 * ksum;
 }
 
 cudaError_t launch_update(const StepParams& P, int ns, double lam, const double* ec0,
@@ -628,7 +659,9 @@ cudaError_t launch_update(const StepParams& P, int ns, double lam, const double*
                           double* kap1, cudaStream_t st) {
     const int b = 256;
     const unsigned g = (unsigned)((P.N + b - 1) / b);
-    if (ns == 1)
+    if (ns == 0)
+        k_update<0><<<g, b, 0, st>>>(P, lam, ec0, n0, E0, eh, nH, sE, fMt, MiU, ec1, n1, E1, kap1);
+    else if (ns == 1)
         k_update<1><<<g, b, 0, st>>>(P, lam, ec0, n0, E0, eh, nH, sE, fMt, MiU, ec1, n1, E1, kap1);
     else
         k_update<3><<<g, b, 0, st>>>(P, lam, ec0, n0, E0, eh, nH, sE, fMt, MiU, ec1, n1, E1, kap1);
@@ -655,6 +688,7 @@ __global__ void k_temperature(const StepParams P, int ns, const double* __restri
                               double* __restrict__ T) {
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= P.N) return;
+    if (ns == 0) { T[c] = P.lte_cT * e[c]; return; }          // LTE
     const double nH = nHa[c], nHe = P.y_he * nH;
     const double nHI = n[c];
     const double nHeI = ns == 3 ? n[P.N + c] : 0.0, nHeII = ns == 3 ? n[2 * P.N + c] : 0.0;
@@ -676,7 +710,7 @@ __global__ void k_check_state(const StepParams P, int ns, const double* __restri
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= P.N) return;
     const double nH = nHa[c], nHe = P.y_he * nH;
-    const double nHI = n[c];
+    const double nHI = ns >= 1 ? n[c] : 0.0;
     const double nHeI = ns == 3 ? n[P.N + c] : 0.0, nHeII = ns == 3 ? n[2 * P.N + c] : 0.0;
     const bool ok = (E[c] > 0.0) && (e[c] > 0.0) && (nH > 0.0) && (nHI >= 0.0) &&
                     (nH - nHI >= 0.0) && (nHeI >= 0.0) && (nHeII >= 0.0) &&
@@ -745,7 +779,8 @@ __global__ void __launch_bounds__(256) k_time_error(const StepParams P, const do
 cudaError_t launch_time_error(const StepParams& P, int ns, const double* ec, const double* n,
                               const double* E, const double* Up, double pn, double* partials,
                               int nblocks, cudaStream_t st) {
-    if (ns == 1) k_time_error<1><<<nblocks, 256, 0, st>>>(P, ec, n, E, Up, pn, partials);
+    if (ns == 0) k_time_error<0><<<nblocks, 256, 0, st>>>(P, ec, n, E, Up, pn, partials);
+    else if (ns == 1) k_time_error<1><<<nblocks, 256, 0, st>>>(P, ec, n, E, Up, pn, partials);
     else k_time_error<3><<<nblocks, 256, 0, st>>>(P, ec, n, E, Up, pn, partials);
     return cudaGetLastError();
 }
