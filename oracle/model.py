@@ -34,6 +34,7 @@ from . import closure as cl
 
 BC_ZERO_FLUX = "zero_flux"
 BC_PERIODIC = "periodic"
+BC_DIRICHLET = "dirichlet"
 
 
 @dataclass
@@ -49,6 +50,7 @@ class Problem:
     grey: dict                         # sk, pgam, ph arrays over (HI, HeI, HeII)
     y_he: float = 0.0                  # n_He / n_H
     bc: tuple = (BC_ZERO_FLUX,) * 6    # faces x-, x+, y-, y+, z-, z+
+    bc_value: tuple = (0.0,) * 6       # E on Dirichlet faces, erg cm^-3
     theta: float = 0.51                # Sec. 3.2, below eq. radiation_simplified
     m_grey: int = 1                    # m of eq. cons_radiation
     isothermal: bool = False           # fixed temperature, e_c == 0 (Sec. 4.5 test setup)
@@ -284,30 +286,33 @@ def _local_terms_lte(p, ec, E, eh, nH, src, a, adot, T_fixed, want_jac):
 # --------------------------------------------------------------------------------------------
 # diffusion (eq. mDE with eq. limiter)
 
-def face_coefficient(p, Ea, Eb, ka, kb, a):
-    """D_face / (a^2 dx^2) for a face between cells a and b (per unit time, 1/s).
+def face_coefficient(p, Ea, Eb, ka, kb, a, h=None):
+    """D_face / (a^2 dx h) for a face between points a and b a distance h apart (default dx:
+    two cells; dx/2: a cell and a Dirichlet boundary value), per unit time, 1/s.
 
     R is floored at 1 / (a L), L the largest comoving extent of the grid, so that D <= c a L
     where the radiation field is flat and the medium transparent (kappa = R = 0 leaves
     eq. limiter undefined).  Without the limiter D = c / (3 max(kappa, kappa_floor))."""
+    h = p.dx if h is None else h
     kap = 0.5 * (ka + kb)
     c = cl.C_LIGHT
     if p.limiter:
         Ebar = 0.5 * (Ea + Eb)
         R_min = 1.0 / (a * max(p.nx, p.ny, p.nz) * p.dx)
-        R = np.maximum(np.abs(Eb - Ea) / (a * p.dx * Ebar), R_min)
+        R = np.maximum(np.abs(Eb - Ea) / (a * h * Ebar), R_min)
         D = c * (2.0 * kap + R) / (6.0 * kap ** 2 + 3.0 * kap * R + R ** 2)   # eq. limiter
     else:
         D = c / (3.0 * np.maximum(kap, p.kappa_floor))
-    return D / (a * a * p.dx * p.dx)
+    return D / (a * a * p.dx * h)
 
 
-def face_coefficient_derivatives(p, Ea, Eb, ka, kb, a):
+def face_coefficient_derivatives(p, Ea, Eb, ka, kb, a, h=None):
     """(W, dW/dE_a, dW/dE_b) of ``face_coefficient`` with kappa held fixed (Sec. 3.2.1 lags
     only the opacity dependence of D).  dD/dR = -c R (4 kappa + R) / (6 kappa^2 + 3 kappa R +
     R^2)^2 and dR/dE_{a,b} = -/+ sign(E_b - E_a) / (a dx Ebar) - R / (2 Ebar); zero where R
     sits at its floor or without the limiter."""
-    W = face_coefficient(p, Ea, Eb, ka, kb, a)
+    h = p.dx if h is None else h
+    W = face_coefficient(p, Ea, Eb, ka, kb, a, h)
     if not p.limiter:
         z = np.zeros_like(W)
         return W, z, z
@@ -315,34 +320,53 @@ def face_coefficient_derivatives(p, Ea, Eb, ka, kb, a):
     c = cl.C_LIGHT
     Ebar = 0.5 * (Ea + Eb)
     R_min = 1.0 / (a * max(p.nx, p.ny, p.nz) * p.dx)
-    Rraw = np.abs(Eb - Ea) / (a * p.dx * Ebar)
+    Rraw = np.abs(Eb - Ea) / (a * h * Ebar)
     live = Rraw > R_min
     R = np.maximum(Rraw, R_min)
     den = 6.0 * kap ** 2 + 3.0 * kap * R + R ** 2
     dDdR = -c * R * (4.0 * kap + R) / den ** 2
     sgn = np.sign(Eb - Ea)
-    dRa = -sgn / (a * p.dx * Ebar) - R / (2.0 * Ebar)
-    dRb = sgn / (a * p.dx * Ebar) - R / (2.0 * Ebar)
-    f = np.where(live, dDdR / (a * a * p.dx * p.dx), 0.0)
+    dRa = -sgn / (a * h * Ebar) - R / (2.0 * Ebar)
+    dRb = sgn / (a * h * Ebar) - R / (2.0 * Ebar)
+    f = np.where(live, dDdR / (a * a * p.dx * h), 0.0)
     return W, f * dRa, f * dRb
 
 
-def face_coefficient_kappa_derivative(p, Ea, Eb, ka, kb, a):
+def face_coefficient_kappa_derivative(p, Ea, Eb, ka, kb, a, h=None):
     """dW/dkappa_face of ``face_coefficient`` at fixed E: with the limiter
     dD/dkappa = -c (12 kappa^2 + 12 kappa R + R^2) / (6 kappa^2 + 3 kappa R + R^2)^2 (the
     quotient rule on eq. limiter), without it -c / (3 kappa^2) above the floor, else 0.  Each
     cell's kappa enters the face mean with weight 1/2."""
+    h = p.dx if h is None else h
     kap = 0.5 * (ka + kb)
     c = cl.C_LIGHT
     if p.limiter:
         Ebar = 0.5 * (Ea + Eb)
         R_min = 1.0 / (a * max(p.nx, p.ny, p.nz) * p.dx)
-        R = np.maximum(np.abs(Eb - Ea) / (a * p.dx * Ebar), R_min)
+        R = np.maximum(np.abs(Eb - Ea) / (a * h * Ebar), R_min)
         den = 6.0 * kap ** 2 + 3.0 * kap * R + R ** 2
         dD = -c * (12.0 * kap ** 2 + 12.0 * kap * R + R ** 2) / den ** 2
     else:
         dD = np.where(kap > p.kappa_floor, -c / (3.0 * np.maximum(kap, p.kappa_floor) ** 2), 0.0)
-    return dD / (a * a * p.dx * p.dx)
+    return dD / (a * a * p.dx * h)
+
+
+def dirichlet_faces(p):
+    """[(d, mask, E_b)] for every Dirichlet face d (0..5 = x-, x+, y-, y+, z-, z+): the cells
+    next to it and the boundary value.  The value sits on the boundary, half a cell from the
+    cell centre."""
+    if BC_DIRICHLET not in p.bc:
+        return []
+    k, j, i = np.meshgrid(np.arange(p.nz), np.arange(p.ny), np.arange(p.nx), indexing="ij")
+    q = (i.ravel(), j.ravel(), k.ravel())
+    dims = (p.nx, p.ny, p.nz)
+    out = []
+    for d in range(6):
+        if p.bc[d] == BC_DIRICHLET:
+            ax = d // 2
+            m = q[ax] == (0 if d % 2 == 0 else dims[ax] - 1)
+            out.append((d, m, float(p.bc_value[d])))
+    return out
 
 
 def diffusion_kappa_block(p, E, kap, a, dth, nbt):
@@ -360,6 +384,10 @@ def diffusion_kappa_block(p, E, kap, a, dth, nbt):
         v = dth * 0.5 * face_coefficient_kappa_derivative(p, E, Enb, kap, knb, a) * (E - Enb)
         diag += np.where(m, v, 0.0)
         rows.append(cells[m]); cols.append(nb[d][m]); vals.append(v[m])
+    for d, m, Eb in dirichlet_faces(p):
+        # the boundary face's opacity is the cell's own (weight 1)
+        v = dth * face_coefficient_kappa_derivative(p, E, Eb, kap, kap, a, 0.5 * p.dx) * (E - Eb)
+        diag += np.where(m, v, 0.0)
     return diag, rows, cols, vals
 
 
@@ -369,6 +397,8 @@ def face_weights(p, E, kap, a, nbt=None):
     W = np.zeros((6, p.N))
     for d in range(6):
         W[d] = np.where(valid[d], face_coefficient(p, E, E[nb[d]], kap, kap[nb[d]], a), 0.0)
+    for d, m, Eb in dirichlet_faces(p):       # boundary faces: distance dx/2, kappa of the cell
+        W[d] = np.where(m, face_coefficient(p, E, Eb, kap, kap, a, 0.5 * p.dx), W[d])
     return W
 
 
@@ -378,6 +408,8 @@ def diffusion_term(p, E, W, nbt=None):
     out = np.zeros(p.N)
     for d in range(6):
         out += np.where(valid[d], W[d] * (E - E[nb[d]]), 0.0)
+    for d, m, Eb in dirichlet_faces(p):
+        out += np.where(m, W[d] * (E - Eb), 0.0)
     return out
 
 
@@ -485,6 +517,13 @@ def diffusion_block(p, E, kap, a, dth, nbt):
             di, off = W, -W
         diag += np.where(m, dth * di, 0.0)
         rows.append(cells[m]); cols.append(nb[d][m]); vals.append(dth * off[m])
+    for d, m, Eb in dirichlet_faces(p):
+        if p.limiter_jacobian in ("E", "exact"):
+            W, dWi, _ = face_coefficient_derivatives(p, E, Eb, kap, kap, a, 0.5 * p.dx)
+            di = W + dWi * (E - Eb)
+        else:
+            di = face_coefficient(p, E, Eb, kap, kap, a, 0.5 * p.dx)
+        diag += np.where(m, dth * di, 0.0)
     return diag, rows, cols, vals
 
 
