@@ -43,7 +43,7 @@ extern "C" {
 #define RHI_ERR_NONPHYSICAL 4   /* non-positive or non-finite state, or a CG breakdown       */
 #define RHI_ERR_STATE 5         /* call order: no state set yet                              */
 
-enum { RHI_BC_ZERO_FLUX = 0, RHI_BC_PERIODIC = 1 };
+enum { RHI_BC_ZERO_FLUX = 0, RHI_BC_PERIODIC = 1, RHI_BC_DIRICHLET = 2 };
 enum { RHI_GUESS_PREVIOUS = 0, RHI_GUESS_PREDICTOR = 1, RHI_GUESS_LEARNED = 2 };
 /* physics model: non-LTE ionization chemistry (Sec. 2.1, n_species 1 or 3), or the LTE
    coupling of eq. LTE_coupling (n_species 0: gas and radiation energy only, constant total
@@ -58,9 +58,14 @@ typedef struct {
     double dx;
 } rhi_grid;
 
-/* Boundary kind per face, order x-, x+, y-, y+, z-, z+; periodic faces come in pairs. */
+/* Boundary kind per face, order x-, x+, y-, y+, z-, z+; periodic faces come in pairs.
+   A Dirichlet face holds the radiation energy density value[d] (erg cm^-3, > 0) on the face,
+   half a cell from the centre of the cell next to it; the flux through it is
+   D (E_b - E) / (a^2 dx dx/2) with the limiter's R over that distance and the cell's
+   opacity.  The gas and species have no boundary fluxes (the path has no hydrodynamics). */
 typedef struct {
     int kind[6];
+    double value[6];
 } rhi_bc;
 
 /* Method and closure parameters.  Fill with rhi_params_default, then override. */
@@ -126,6 +131,8 @@ typedef struct {
     int guess_used;         /* RHI_GUESS_* actually used (learned falls back to previous)    */
     int launches;           /* kernel launches of the last step                              */
     int guess_restarts;     /* 1 when Newton abandoned the learned start for U^n (mlp_restart) */
+    int krylov_fallbacks;   /* Newton iterations whose BiCGStab broke down and that took the
+                               lagged-D direction (CG) instead                              */
     double res_initial;     /* ||f(U_0)|| (eq. rmsnorm, scaled)                              */
     double res_final;       /* ||f(U^{n+1})||                                                */
     double res_guess_prev;  /* ||f(U^n)|| when a learned guess was tried, else 0             */
@@ -221,8 +228,8 @@ int rhi_kernel_times(rhi_handle h, int max, char* names, double* total_ms, int* 
 /* Adaptive time stepping (Sec. 3.2.3; needs params.dt_norm != 0): implicit steps from the
    current state until t_end, the first of length dt0, each later one the dt_next of its
    predecessor, clamped to [dt_min, dt_max] and to the time left.  A step whose Newton
-   iteration fails is retried with half the step (the state is unchanged by a failed step),
-   down to dt_min.  Writes the time reached and the number of steps taken; returns RHI_OK, or
+   iteration fails (no convergence, a non-physical iterate or a Krylov breakdown) is retried
+   with half the step (the state is unchanged by a failed step), down to dt_min.  Writes the time reached and the number of steps taken; returns RHI_OK, or
    the error of a step that failed at dt_min, or RHI_ERR_NONCONVERGED after max_steps steps
    short of t_end. */
 int rhi_advance(rhi_handle h, double t_end, double dt0, double dt_min, double dt_max, double a,

@@ -14,7 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librhi.so")
 
 RHI_OK, RHI_ERR_ARG, RHI_ERR_CUDA, RHI_ERR_NONCONVERGED, RHI_ERR_NONPHYSICAL, RHI_ERR_STATE = range(6)
-RHI_BC_ZERO_FLUX, RHI_BC_PERIODIC = 0, 1
+RHI_BC_ZERO_FLUX, RHI_BC_PERIODIC, RHI_BC_DIRICHLET = 0, 1, 2
 RHI_GUESS_PREVIOUS, RHI_GUESS_PREDICTOR, RHI_GUESS_LEARNED = 0, 1, 2
 RHI_PRECOND_JACOBI, RHI_PRECOND_MG_FP64, RHI_PRECOND_MG_FP32 = 0, 1, 2
 RHI_SPECTRUM_MONO, RHI_SPECTRUM_BLACKBODY, RHI_SPECTRUM_POWERLAW = 0, 1, 2
@@ -26,7 +26,7 @@ class rhi_grid(C.Structure):
 
 
 class rhi_bc(C.Structure):
-    _fields_ = [("kind", C.c_int * 6)]
+    _fields_ = [("kind", C.c_int * 6), ("value", C.c_double * 6)]
 
 
 class rhi_params(C.Structure):
@@ -47,7 +47,7 @@ class rhi_params(C.Structure):
 class rhi_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("newton_its", C.c_int), ("pcg_its", C.c_int),
                 ("vcycles", C.c_int), ("backtracks", C.c_int), ("lam_min_steps", C.c_int),
-                ("guess_used", C.c_int), ("launches", C.c_int), ("guess_restarts", C.c_int),
+                ("guess_used", C.c_int), ("launches", C.c_int), ("guess_restarts", C.c_int), ("krylov_fallbacks", C.c_int),
                 ("res_initial", C.c_double),
                 ("res_final", C.c_double), ("res_guess_prev", C.c_double), ("ms", C.c_double),
                 ("eps_loc", C.c_double), ("dt_next", C.c_double),
@@ -183,11 +183,13 @@ def _ptr(a):
 class Solver:
     """One rhi handle: grid, boundaries and parameters fixed at creation."""
 
-    def __init__(self, nx, ny, nz, dx, params, bc=(RHI_BC_ZERO_FLUX,) * 6, stream=None):
+    def __init__(self, nx, ny, nz, dx, params, bc=(RHI_BC_ZERO_FLUX,) * 6, stream=None,
+                 bc_value=(0.0,) * 6):
         self.grid = rhi_grid(nx, ny, nz, dx)
         b = rhi_bc()
         for q in range(6):
             b.kind[q] = int(bc[q])
+            b.value[q] = float(bc_value[q])
         self.bc = b
         self.params = params
         self.ns = params.n_species
@@ -409,8 +411,10 @@ def params_for_workload(w, **overrides):
 def solver_for_workload(w, stream=None, sources=True, **overrides):
     """A Solver holding the workload's initial state and point sources (host marshalling)."""
     p = params_for_workload(w, **overrides)
-    bc = [RHI_BC_PERIODIC if b == "periodic" else RHI_BC_ZERO_FLUX for b in w.bc]
-    s = Solver(w.nx, w.ny, w.nz, w.dx, p, bc=bc, stream=stream)
+    kinds = {"zero_flux": RHI_BC_ZERO_FLUX, "periodic": RHI_BC_PERIODIC,
+             "dirichlet": RHI_BC_DIRICHLET}
+    bc = [kinds[b] for b in w.bc]
+    s = Solver(w.nx, w.ny, w.nz, w.dx, p, bc=bc, stream=stream, bc_value=w.bc_value)
     st = w.state()
     s.set_state(st["E"], st["e"], np.ascontiguousarray(st["n"]).ravel() if w.ns else None,
                 np.ascontiguousarray(w.nH.ravel()))

@@ -186,6 +186,11 @@ StepParams make_params(const rhi_ctx* h, double dt, double a, double adot) {
     P.fd_nxy = make_fastdiv((unsigned)P.nx * (unsigned)P.ny);
     P.N = h->N;
     P.per_x = h->per[0]; P.per_y = h->per[1]; P.per_z = h->per[2];
+    P.dir_mask = 0;
+    for (int d = 0; d < 6; ++d) {
+        P.Eb[d] = h->bc.value[d];
+        if (h->bc.kind[d] == RHI_BC_DIRICHLET) P.dir_mask |= 1 << d;
+    }
     P.dx = h->grid.dx;
     P.a = a; P.ia3 = 1.0 / (a * a * a); P.adot_a = adot / a;
     P.dt = dt; P.dth = dt * h->prm.theta; P.dtm1 = dt * (h->prm.theta - 1.0);
@@ -480,6 +485,7 @@ int pcg(rhi_ctx* h, const double* rhs, double tol, int* its_out) {
     const long long N = h->N;
     const double norm = 1.0 / ((double)N * h->nv);
     int np = 0;
+    CK(cudaMemsetAsync(h->scal + S_BREAK, 0, sizeof(double), h->st));     // clear an old breakdown
     CK(L.cg_init(N, rhs, h->r, h->x, h->partials, np));
     CK(L.reduce(h->partials, np, h->scal, RED_SUM, S_RR));
     double rr;
@@ -517,6 +523,7 @@ int bicgstab(rhi_ctx* h, const double* rhs, double tol, int* its_out) {
     const long long N = h->N;
     const double norm = 1.0 / ((double)N * h->nv);
     int np = 0;
+    CK(cudaMemsetAsync(h->scal + S_BREAK, 0, sizeof(double), h->st));     // clear an old breakdown
     CK(L.bicg_init(N, rhs, h->r, h->rh, h->x, h->partials, np));
     CK(L.reduce(h->partials, np, h->scal, RED_SUM, S_RR));
     double rr;
@@ -778,9 +785,13 @@ int rhi_create(const rhi_grid* grid, const rhi_bc* bc, const rhi_params* params,
     if (N > (1LL << 31)) return RHI_ERR_ARG;
     for (int a = 0; a < 3; ++a) {
         const int lo = bc->kind[2 * a], hi = bc->kind[2 * a + 1];
-        if ((lo != RHI_BC_ZERO_FLUX && lo != RHI_BC_PERIODIC) ||
-            (hi != RHI_BC_ZERO_FLUX && hi != RHI_BC_PERIODIC) || (lo == RHI_BC_PERIODIC) != (hi == RHI_BC_PERIODIC))
+        if (lo < RHI_BC_ZERO_FLUX || lo > RHI_BC_DIRICHLET || hi < RHI_BC_ZERO_FLUX ||
+            hi > RHI_BC_DIRICHLET || (lo == RHI_BC_PERIODIC) != (hi == RHI_BC_PERIODIC))
             return RHI_ERR_ARG;
+        for (int s = 0; s < 2; ++s)
+            if (bc->kind[2 * a + s] == RHI_BC_DIRICHLET &&
+                !(bc->value[2 * a + s] > 0.0 && std::isfinite(bc->value[2 * a + s])))
+                return RHI_ERR_ARG;
     }
     if (!validate_params(params)) return RHI_ERR_ARG;
 
@@ -1225,7 +1236,16 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
         int its = 0;
         if (h->prm.limiter_jacobian) {
             set_opns(h, P, set, h->PQ[cur < 0 ? 0 : cur]);
-            if ((rc = bicgstab(h, h->rhs[set], lin_tol * res, &its))) { S.status = rc; return rc; }
+            rc = bicgstab(h, h->rhs[set], lin_tol * res, &its);
+            if (rc == RHI_ERR_NONPHYSICAL) {
+                // BiCGStab broke down (where free streaming makes the advective part of the
+                // matrix dominate): this Newton iteration takes the direction of the
+                // symmetric lagged-D matrix instead, solved by CG
+                S.krylov_fallbacks += 1;
+                S.pcg_its += its;
+                rc = pcg(h, h->rhs[set], lin_tol * res, &its);
+            }
+            if (rc) { S.status = rc; return rc; }
         } else if ((rc = pcg(h, h->rhs[set], lin_tol * res, &its))) {
             S.status = rc;
             return rc;
@@ -1342,7 +1362,8 @@ int rhi_advance(rhi_handle h, double t_end, double dt0, double dt_min, double dt
     while (t < t_end * (1.0 - 1e-12) && n < max_steps) {
         double d = std::min(dt, t_end - t);
         rc = rhi_implicit_step(h, d, a, adot, newton_tol, lin_tol);
-        while (rc == RHI_ERR_NONCONVERGED && 0.5 * d >= dt_min && 0.5 * d > 0.0) {
+        while ((rc == RHI_ERR_NONCONVERGED || rc == RHI_ERR_NONPHYSICAL) && 0.5 * d >= dt_min &&
+               0.5 * d > 0.0) {
             d *= 0.5;                           // the state is unchanged by a failed step
             rc = rhi_implicit_step(h, d, a, adot, newton_tol, lin_tol);
         }

@@ -44,6 +44,8 @@ struct StepParams {
     long long N;
     FastDiv fd_nx, fd_nxy;            // division by nx and nx * ny
     int per_x, per_y, per_z;          // periodic axes
+    int dir_mask;                     // bit d: face d (x-, x+, y-, y+, z-, z+) is Dirichlet
+    double Eb[6];                     // E on the Dirichlet faces
     double dx;
     double a, ia3, adot_a;            // a, 1/a^3, adot / a
     double dt, dth, dtm1;             // dt, dt theta, dt (theta - 1)

@@ -99,6 +99,40 @@ __device__ __forceinline__ FaceCoef face_coef(const StepParams& P, double Ea, do
     return r;
 }
 
+// A Dirichlet face: the boundary value E_b sits on the face, half a cell from the centre, and
+// the face's opacity is the cell's.  The coefficient is D / (a^2 dx dx/2) with R over that
+// half-cell distance (s = a (dx/2) Ebar); Qd is the cell's Newton-diagonal entry
+// W - dW/dE_c (E_b - E_c) and dWdk = dW/dkappa (exact matrix).
+struct BoundaryFace { double W, Qd, dWdk; };
+
+__device__ __forceinline__ BoundaryFace boundary_face(const StepParams& P, double E, double Eb,
+                                                      double kap) {
+    BoundaryFace r;
+    if (P.limiter) {
+        const double Esum = E + Eb;
+        const double s = 0.5 * Esum * P.half_adx;
+        const double dE = Eb - E;
+        const double qraw = fabs(dE);
+        const double q = fmax(qraw, P.R_min * s);
+        const double ks = kap * s;
+        const double den = 6.0 * ks * ks + 3.0 * ks * q + q * q;
+        const double iden = 1.0 / den;
+        r.W = 2.0 * C_LIGHT * s * (2.0 * ks + q) * iden * P.inv_a2dx2;
+        r.Qd = r.W;
+        if (P.limiter_newton >= 1 && qraw > P.R_min * s) {
+            const double X = -2.0 * C_LIGHT * q * q * (4.0 * ks + q) * iden * iden * P.inv_a2dx2;
+            r.Qd = r.W + X * s + X * dE * 0.5 * P.half_adx;
+        }
+        r.dWdk = -2.0 * C_LIGHT * s * s * (12.0 * ks * ks + 12.0 * ks * q + q * q) * iden * iden *
+                 P.inv_a2dx2;
+        return r;
+    }
+    r.W = 2.0 * C_LIGHT / (3.0 * fmax(kap, P.kappa_floor)) * P.inv_a2dx2;
+    r.Qd = r.W;
+    r.dWdk = kap > P.kappa_floor ? -r.W / kap : 0.0;
+    return r;
+}
+
 template <int JM>
 __global__ void __launch_bounds__(256) k_faces(const StepParams P, const double* __restrict__ E,
                                                const double* __restrict__ kap,
@@ -473,9 +507,44 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const P
                 if (nb.has_hi[ax]) PQsum += B.PQ[(3 + ax) * N + nb.hi[ax]];
             }
         }
+        // Dirichlet faces of boundary cells (they carry no entry in the face arrays)
+        double kb_term = 0.0;
+        if (P.dir_mask) {
+            const int q[3] = {i, j, k};
+            const int ext[3] = {P.nx, P.ny, P.nz};
+            // the cell's opacity at this iterate (the same sum as k_kappa)
+            double kc;
+            if constexpr (NS == 0) {
+                kc = P.kappa_total;
+            } else {
+                double sk = P.sk[0] * n[0];
+                if constexpr (NS == 3) sk += P.sk[1] * n[1] + P.sk[2] * n[2];
+                kc = P.ia3 * sk;
+            }
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+                const int ax = d >> 1;
+                if ((P.dir_mask >> d & 1) && q[ax] == ((d & 1) ? ext[ax] - 1 : 0)) {
+                    const double Eb = P.Eb[d];
+                    const BoundaryFace bf = boundary_face(P, E, Eb, kc);
+                    Dterm += bf.W * (E - Eb);
+                    Wsum += bf.W;
+                    PQsum += bf.Qd;
+                    kb_term += bf.dWdk * (E - Eb);
+                }
+            }
+        }
 
         Local<NS> lo;
         local_model<NS, MODE != MODE_PREP_PREDICT>(P, ec, n, E, eh, nH, src, Tfix, lo);
+        if constexpr (NS > 0 && MODE != MODE_PREP_PREDICT) {
+            // exact matrix: a Dirichlet face's opacity is the cell's, so its kappa derivative
+            // joins the cell's own E-row species entries
+            if (P.limiter_newton == 2 && kb_term != 0.0) {
+#pragma unroll
+                for (int X = 0; X < NS; ++X) lo.dLEx[1 + X] += kb_term * P.ia3 * P.sk[X];
+            }
+        }
         double Lf[NV];
 #pragma unroll
         for (int v = 0; v <= NS; ++v) Lf[v] = lo.L[v];

@@ -54,6 +54,7 @@ class Workload:
     u_n: float = 1.0
     u_E: float = 1.0
     bc: tuple = ("zero_flux",) * 6
+    bc_value: tuple = (0.0,) * 6  # E on Dirichlet faces, erg cm^-3
     meta: dict = field(default_factory=dict)
     schedule: list = None       # per step (dt, a, adot), cosmological runs
     model: str = "ionization"   # "ionization" (species) or "lte" (ns = 0, constant opacities)

@@ -22,6 +22,7 @@ def oracle_problem(w, **overrides):
     src = cl.deposit_sources(w.nH.shape, w.dx, w.src_ijk, w.src_rate, grey["eps"])
     args = dict(nx=w.nx, ny=w.ny, nz=w.nz, dx=w.dx, ns=w.ns, nH=w.nH, src=src, grey=grey,
                 y_he=w.y_he, bc=w.bc, theta=w.theta, u_e=w.u_e, u_n=w.u_n, u_E=w.u_E,
-                model=w.model, kappa_total=w.kappa_total, kappa_planck=w.kappa_planck, mu=w.mu)
+                model=w.model, kappa_total=w.kappa_total, kappa_planck=w.kappa_planck, mu=w.mu,
+                bc_value=w.bc_value)
     args.update(overrides)
     return md.Problem(**args)

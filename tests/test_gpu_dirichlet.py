@@ -1,0 +1,107 @@
+"""Dirichlet radiation boundaries on the GPU: steps vs the FP64 oracle in both physics models and
+all three Newton matrices, the steady diffusion line between two boundary values, and the
+free-streaming front of Sec. 4.2, which the limiter must move at the speed of light."""
+import numpy as np
+import pytest
+
+from conftest import oracle_problem
+from oracle import closure as cl, solve as sv
+from paper_0901_1110_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+KPC = inputs.KPC
+BCD = ("dirichlet", "dirichlet", "zero_flux", "zero_flux", "periodic", "periodic")
+
+
+@pytest.fixture(scope="module")
+def rhi():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_0901_1110_gb300 import _build
+    _build.build()
+    import paper_0901_1110_gb300 as rhi
+    rhi.lib()
+    return rhi
+
+
+def _close(g, ref, keys):
+    for key in keys:
+        a = np.asarray(g[key]).reshape(np.shape(ref[key]))
+        assert np.abs(a - ref[key]).max() <= 1e-10 * np.abs(ref[key]).max(), key
+
+
+@pytest.mark.parametrize("ljac", [0, 1, 2])
+def test_ionization_steps_with_dirichlet_faces_match_oracle(rhi, ljac):
+    w = inputs.uniform_h(6, shape=(5, 6, 7), box=60 * KPC, dt=3e12, E0=1e-19, bc=BCD)
+    w.bc_value = (5e-16, 1e-18, 0.0, 0.0, 0.0, 0.0)
+    w.theta = 1.0
+    w.u_E = 1e-17
+    s = rhi.solver_for_workload(w, limiter_jacobian=ljac, precond=rhi.RHI_PRECOND_MG_FP32,
+                                mg_levels=3)
+    p = oracle_problem(w)
+    ref = w.state()
+    for _ in range(3):
+        s.step(w.dt, newton_tol=1e-12, lin_tol=1e-12)
+        ref, info = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, 1e-13, linear="direct")
+        assert info["converged"]
+        _close(s.get_state(), ref, ("E", "e", "n"))
+
+
+def test_lte_steps_with_dirichlet_faces_match_oracle(rhi):
+    w = inputs.lte_uniform(7e7, n=6, box=3e11, E_perturb=0.2, dt=3e-10, bc=BCD)
+    w.bc_value = (3e12, 2e11, 0.0, 0.0, 0.0, 0.0)
+    s = rhi.solver_for_workload(w, limiter_jacobian=2, precond=rhi.RHI_PRECOND_MG_FP32,
+                                mg_levels=2)
+    p = oracle_problem(w)
+    ref = w.state()
+    for _ in range(3):
+        s.step(w.dt, newton_tol=1e-12, lin_tol=1e-12)
+        ref, info = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, 1e-13, linear="direct")
+        assert info["converged"]
+        _close(s.get_state(), ref, ("E", "e"))
+
+
+def test_steady_diffusion_line_on_gpu(rhi):
+    n, L = 16, 1.0
+    bc = ("dirichlet", "dirichlet", "zero_flux", "zero_flux", "zero_flux", "zero_flux")
+    w = inputs.lte_uniform(1.0, n=n, rho=1.0, E0=0.5, kappa=1e-6, box=L, dt=1e-14, bc=bc)
+    w.kappa_planck = 0.0
+    w.bc_value = (2.0, 1.0, 0.0, 0.0, 0.0, 0.0)
+    s = rhi.solver_for_workload(w, limiter=0, u_e=1.0, u_E=1.0,
+                                precond=rhi.RHI_PRECOND_MG_FP64, mg_levels=3)
+    for _ in range(4):
+        s.step(1e-14, newton_tol=1e-10, lin_tol=1e-12)
+    x = (np.arange(n) + 0.5) * (L / n)
+    E = np.asarray(s.get_state()["E"]).reshape(n, n, n)
+    assert np.abs(E - (2.0 - x / L)[None, None, :]).max() < 1e-9
+
+
+@pytest.mark.timeout(300)
+def test_free_streaming_front_moves_at_c(rhi):
+    """Sec. 4.2: a 1 cm line of 128 cells, opacity 1e-6 cm^-1 (Planck and total), E = 1e-4,
+    E = 1 held on the left face; after a quarter of the light-crossing time (8.3391 ps) the
+    front, where E falls through one half, sits at c t = 0.25 cm to within the few cells the
+    paper's adaptive steps also lag by."""
+    n = 128
+    bc = ("dirichlet", "zero_flux", "zero_flux", "zero_flux", "zero_flux", "zero_flux")
+    w = inputs.lte_uniform(1e-6, n=1, rho=1e-3, E0=1e-4, kappa=1e-6, box=1.0, bc=bc)
+    # a line of n cells along x
+    w.nx, w.ny, w.nz = n, 1, 1
+    w.dx = 1.0 / n
+    for f in ("nH", "E", "e"):
+        setattr(w, f, np.full((1, 1, n), getattr(w, f).ravel()[0]))
+    w.n = np.zeros((0, 1, 1, n))
+    w.bc_value = (1.0, 0.0, 0.0, 0.0, 0.0, 0.0)
+    w.u_E = 1.0
+    # exact matrix; where its BiCGStab breaks down (the advective part of the matrix dominates
+    # in free streaming) a Newton iteration takes the lagged-D direction with CG
+    s = rhi.solver_for_workload(w, limiter_jacobian=2, dt_norm=-1, dt_tau_tol=0.05,
+                                precond=rhi.RHI_PRECOND_MG_FP64, mg_levels=4, max_newton=50)
+    t_end = 0.25 / cl.C_LIGHT
+    t, steps = s.advance(t_end, 1e-15, dt_min=1e-18, newton_tol=1e-6, lin_tol=1e-8)
+    E = np.asarray(s.get_state()["E"])
+    x = (np.arange(n) + 0.5) / n
+    front = x[np.argmax(E < 0.5)]
+    print(f"front at {front:.4f} cm after {steps} steps (c t = 0.25 cm)")
+    assert abs(front - 0.25) < 0.03
+    assert E[0] > 0.9 and E[-1] < 1e-3
