@@ -44,16 +44,16 @@ def load_peaks():
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 
 # FP64 flops per cell of the fused cell kernels (bound by the FP64 pipe, about 1.2 TFLOP/s here),
-# counted by ncu as 2 DFMA + DMUL + DADD thread instructions per cell (177, 113, 78 on the
+# counted by ncu as 2 DFMA + DMUL + DADD thread instructions per cell (175, 106, 76 on the
 # H + He lognormal 128^3 case)
 ALU_FLOPS = {
-    "cell_residual_schur": 545,
+    "cell_residual_schur": 532,
 }
 # DRAM bytes per launch (read + write) from ncu, per cell of the 128^3 capture times the cells
 # of the timed grid (the kernel streams every field once, so traffic grows with the cells);
 # remove an entry when its kernel changes
 TRAFFIC_PER_CELL = {
-    "cell_residual_schur": 522.2e6 / 128 ** 3,
+    "cell_residual_schur": 521.9e6 / 128 ** 3,
 }
 # launches bracketed by events inside the timed region
 # (the FP32 V-cycle replays as one CUDA graph, so its kernels are not bracketed one by one)
