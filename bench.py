@@ -81,12 +81,27 @@ ALG_BYTES = {
     "cg_matvec_dot": 8 * (1 + 3 + 1) + 8,
     "cg_update_xr": 8 * 4 + 8 * 2,
     "cg_update_p": 8 * 2 + 8,
+    # BiCGStab (exact Newton matrix): y = A x reads x, diag, P and Q of 3 faces, the dot's
+    # vector; writes y
+    "bicg_matvec": 8 * (1 + 1 + 3 + 3 + 1) + 8,
+    "bicg_update_xr": 8 * 6 + 8 * 2,
+    "bicg_update_p": 8 * 3 + 8,
+    "bicg_update_s": 8 * 2 + 8,
     "kappa": 8 * 3 + 8,
-    # weighted-Jacobi sweep on the finest level: x, b, diag, 3 lower faces read, x written
-    # (the first sweep of a cycle starts from x = 0 and reads no x): 2 + 2 sweeps average
-    "mg_smooth_f32_fine": (4 * 6 + 3 * 4 * 7) / 4,
-    "mg_smooth_f64_fine": (8 * 6 + 3 * 8 * 7) / 4,
+    # weighted-Jacobi sweep on the finest level: x, b, omega / diag, 3 lower faces read, x
+    # written; the first sweep of a cycle starts from x = 0 and reads b and omega / diag
+    # only: the 1 + 3 sweeps of a 2 + 2 cycle average
+    "mg_smooth_f32_fine": (4 * 3 + 3 * 4 * 7) / 4,
+    "mg_smooth_f64_fine": (8 * 3 + 3 * 8 * 7) / 4,
+    # FP64 Krylov vector to the FP32 right-hand side, and back with the dot r.z
+    "mg_to_f32": 8 + 4,
+    "mg_from_f32_dot": 4 + 8 + 8,
 }
+# the stencil / vector kernels of the Krylov solver and the multigrid preconditioner whose HBM
+# fraction is reported per form
+LINEAR_KERNELS = ("cg_matvec_dot", "cg_update_xr", "cg_update_p", "bicg_matvec",
+                  "bicg_update_xr", "bicg_update_p", "bicg_update_s", "mg_smooth_f32_fine",
+                  "mg_smooth_f64_fine", "mg_to_f32", "mg_from_f32_dot")
 
 
 class ClockSampler:
@@ -457,12 +472,18 @@ def main():
                         frac=ach / hbm_peak,
                         traffic=TRAFFIC_PER_CELL[tname] * w.N if tname in TRAFFIC_PER_CELL else None,
                         peak_source=peak_src)
-    # HBM fraction of the FP64 CG stencil / vector kernels (one full-grid launch each)
-    lin = {}
-    for k in ("cg_matvec_dot", "cg_update_xr", "cg_update_p"):
-        if k in kt:
-            ms_k, c_k = kt[k]
-            lin[k] = ALG_BYTES[k] * w.N / (ms_k / c_k * 1e-3) / 1e9 / hbm_peak
+    # HBM fraction of the Krylov / multigrid stencil and vector kernels (full-grid launches):
+    # algorithmic bytes over the mean launch time of the profiled step, against the measured
+    # copy bandwidth
+    def hbm_fracs(kt_f):
+        out = {}
+        for k in LINEAR_KERNELS:
+            if k in kt_f and kt_f[k][1] > 0 and kt_f[k][0] > 0:
+                ms_k, c_k = kt_f[k]
+                out[k] = ALG_BYTES[k] * w.N / (ms_k / c_k * 1e-3) / 1e9 / hbm_peak
+        return out
+
+    lin = hbm_fracs(kt)
 
     def summary(f):
         return {"value": world * w.N * args.steps / (f["ms"] * 1e-3),
@@ -470,7 +491,8 @@ def main():
                 **{k: v / args.steps for k, v in f["agg"].items()
                    if isinstance(v, (int, float))},
                 "kernel_ms_breakdown_step": {k: v[0] for k, v in
-                                             sorted(f["kt"].items(), key=lambda kv: -kv[1][0])}}
+                                             sorted(f["kt"].items(), key=lambda kv: -kv[1][0])},
+                "hbm_frac": hbm_fracs(f["kt"])}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

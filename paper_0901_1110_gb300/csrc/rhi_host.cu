@@ -75,6 +75,7 @@ struct Level {
     int nx = 0, ny = 0, nz = 0;
     long long N = 0;
     T* diag = nullptr;
+    T* wid = nullptr;           // omega / diag (smoother)
     T* W[3] = {nullptr, nullptr, nullptr};
     T* b = nullptr;
     T* x = nullptr;
@@ -278,6 +279,7 @@ int mg_build_levels(rhi_ctx* h) {
                 if ((rc = dalloc(h, &v.x, v.N))) return rc;
             }
             if ((rc = dalloc(h, &v.xt, v.N))) return rc;
+            if ((rc = dalloc(h, &v.wid, v.N))) return rc;
         }
     } else if (h->prm.precond == RHI_PRECOND_MG_FP32) {
         h->mg32.resize(nl);
@@ -287,6 +289,7 @@ int mg_build_levels(rhi_ctx* h) {
             v.N = (long long)v.nx * v.ny * v.nz;
             int rc;
             if ((rc = dalloc(h, &v.diag, v.N))) return rc;
+            if ((rc = dalloc(h, &v.wid, v.N))) return rc;
             for (int a = 0; a < 3; ++a) if ((rc = dalloc(h, &v.W[a], v.N))) return rc;
             if ((rc = dalloc(h, &v.b, v.N))) return rc;
             if ((rc = dalloc(h, &v.x, v.N))) return rc;
@@ -304,6 +307,7 @@ Op<T> level_op(const rhi_ctx* h, const Level<T>& v) {
     A.fd_nxy = make_fastdiv((unsigned)v.nx * (unsigned)v.ny);
     for (int a = 0; a < 3; ++a) { A.per[a] = h->per[a]; A.W[a] = v.W[a]; }
     A.diag = v.diag;
+    A.wid = v.wid;
     A.scale = T(1);
     return A;
 }
@@ -311,17 +315,21 @@ Op<T> level_op(const rhi_ctx* h, const Level<T>& v) {
 // coarse operators for the current finest operator h->op0
 int precond_setup(rhi_ctx* h) {
     LinLaunch L(h->st, &h->prof);
+    const double om = h->prm.mg_omega;
     if (h->prm.precond == RHI_PRECOND_MG_FP64) {
         auto& lv = h->mg64;
+        h->op0.wid = lv[0].wid;
+        CK(L.inv_diag<double>(h->N, h->op0.diag, om, lv[0].wid));
         for (size_t l = 0; l + 1 < lv.size(); ++l) {
             Op<double> A = (l == 0) ? h->op0 : level_op(h, lv[l]);
             auto& c = lv[l + 1];
             CK((L.coarsen<double, double>(A, c.nx, c.ny, c.nz, c.diag, c.W[0], c.W[1], c.W[2])));
             CK(L.diag_faces<double>(level_op(h, c), c.diag));
+            CK(L.inv_diag<double>(c.N, c.diag, om, c.wid));
         }
     } else if (h->prm.precond == RHI_PRECOND_MG_FP32) {
         auto& lv = h->mg32;
-        CK(L.cast_op(h->op0, lv[0].diag, lv[0].W[0], lv[0].W[1], lv[0].W[2]));
+        CK(L.cast_op(h->op0, om, lv[0].diag, lv[0].W[0], lv[0].W[1], lv[0].W[2], lv[0].wid));
         for (size_t l = 0; l + 1 < lv.size(); ++l) {
             auto& c = lv[l + 1];
             if (l == 0)
@@ -329,6 +337,7 @@ int precond_setup(rhi_ctx* h) {
             else
                 CK((L.coarsen<float, float>(level_op(h, lv[l]), c.nx, c.ny, c.nz, c.diag, c.W[0], c.W[1], c.W[2])));
             CK(L.diag_faces<float>(level_op(h, c), c.diag));
+            CK(L.inv_diag<float>(c.N, c.diag, (float)om, c.wid));
         }
     }
     return RHI_OK;

@@ -40,10 +40,11 @@ __device__ __forceinline__ void coords_fd(long long c, const FastDiv& fx, const 
     i = (int)(r - jj * fx.d);
 }
 
-// (A x)_c with the six neighbours of c
+// sum over the six neighbours of c of W_face x_neighbour (the off-diagonal part of row c
+// before the scale)
 template <typename T, typename TX>
-__device__ __forceinline__ T apply_row(const Op<T>& A, const TX* __restrict__ x, long long c,
-                                       int i, int j, int k, T xc) {
+__device__ __forceinline__ T off_row(const Op<T>& A, const TX* __restrict__ x, long long c,
+                                     int i, int j, int k) {
     const long long sx = 1, sy = A.nx, sz = (long long)A.nx * A.ny;
     const int n[3] = {A.nx, A.ny, A.nz};
     const int q[3] = {i, j, k};
@@ -63,7 +64,21 @@ __device__ __forceinline__ T apply_row(const Op<T>& A, const TX* __restrict__ x,
         off += wlo * T(x[lo]);
         if (has_hi) off += A.W[ax][hi] * T(x[hi]);
     }
-    return A.diag[c] * xc - A.scale * off;
+    return off;
+}
+
+// (A x)_c with the six neighbours of c
+template <typename T, typename TX>
+__device__ __forceinline__ T apply_row(const Op<T>& A, const TX* __restrict__ x, long long c,
+                                       int i, int j, int k, T xc) {
+    return A.diag[c] * xc - A.scale * off_row(A, x, c, i, j, k);
+}
+
+// one weighted-Jacobi update of cell c from the off-diagonal sum:
+// x + omega (b - A x) / diag = (1 - omega) x + (omega / diag) (b + scale off)
+template <typename T>
+__device__ __forceinline__ T jacobi_update(T xc, T b, T wi, T scale, T off, T omega) {
+    return (T(1) - omega) * xc + wi * (b + scale * off);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -226,11 +241,11 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce(const double* __restrict__
 // ---------------------------------------------------------------------------------------------
 // BiCGStab building blocks (FP64), right preconditioning
 
-// y = A x with the non-symmetric operator; partials w1.y (and y.y when two_dots)
+// y = A x with the non-symmetric operator; partials w1.y (and y.y when TWO)
+template <bool TWO>
 __global__ void __launch_bounds__(LIN_BLOCK) k_matvec_ns(const OpNS A, const double* __restrict__ x,
                                                          double* __restrict__ y,
                                                          const double* __restrict__ w1,
-                                                         int two_dots,
                                                          double* __restrict__ partials) {
     double d1 = 0.0, d2 = 0.0;
     const long long sz = (long long)A.nx * A.ny;
@@ -254,11 +269,11 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_matvec_ns(const OpNS A, const dou
         const double v = A.diag[c] * x[c] - A.scale * off;
         y[c] = v;
         d1 += w1[c] * v;
-        d2 += v * v;
+        if (TWO) d2 += v * v;
     }
     const double s1 = block_sum<LIN_BLOCK>(d1);
     if (threadIdx.x == 0) partials[blockIdx.x] = s1;
-    if (two_dots) {
+    if (TWO) {
         const double s2 = block_sum<LIN_BLOCK>(d2);
         if (threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = s2;
     }
@@ -351,8 +366,8 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_axpy(long long N, const double* _
 // ---------------------------------------------------------------------------------------------
 // multigrid kernels (templated on the level precision)
 
-// weighted Jacobi: first sweep from x = 0: x_out = omega b / diag; else
-// x_out = x_in + omega (b - A x_in) / diag
+// weighted Jacobi with wid = omega / diag: first sweep from x = 0: x_out = wid b; else
+// x_out = x_in + omega (b - A x_in) / diag, written as (1 - omega) x_in + wid (b + scale off)
 template <typename T>
 __global__ void __launch_bounds__(LIN_BLOCK) k_mg_smooth(const Op<T> A, const T* __restrict__ b,
                                                          const T* __restrict__ xin,
@@ -360,15 +375,14 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_smooth(const Op<T> A, const T*
                                                          int first) {
     for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < A.N;
          c += (long long)gridDim.x * LIN_BLOCK) {
-        const T d = A.diag[c];
+        const T wi = A.wid[c];
         if (first) {
-            xout[c] = omega * b[c] / d;
+            xout[c] = wi * b[c];
         } else {
             int i, j, k;
             coords3(A, c, i, j, k);
-            const T xc = xin[c];
-            const T ax = apply_row(A, xin, c, i, j, k, xc);
-            xout[c] = xc + omega * (b[c] - ax) / d;
+            const T off = off_row(A, xin, c, i, j, k);
+            xout[c] = jacobi_update(xin[c], b[c], wi, A.scale, off, omega);
         }
     }
 }
@@ -402,7 +416,7 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_smooth_zm(const Op<T> A, const
     const T* __restrict__ W0 = A.W[0];
     const T* __restrict__ W1 = A.W[1];
     const T* __restrict__ W2 = A.W[2];
-    const T* __restrict__ dg = A.diag;
+    const T* __restrict__ wd = A.wid;
     // z: plane below k0 (the far side when k0 = 0: W = 0 there unless periodic).  All loads of
     // the ZM planes are issued first (registers), then the planes are computed in order;
     // the launcher uses this kernel only when ZM divides nz.
@@ -426,7 +440,7 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_smooth_zm(const Op<T> A, const
         x1l[kk] = __ldg(xin + c + dlo1);
         w1h[kk] = hhi1 ? __ldg(W1 + c + dhi1) : T(0);
         x1h[kk] = hhi1 ? __ldg(xin + c + dhi1) : T(0);
-        dd[kk] = __ldg(dg + c);
+        dd[kk] = __ldg(wd + c);
         bb[kk] = __ldg(b + c);
     }
 #pragma unroll
@@ -439,10 +453,7 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_smooth_zm(const Op<T> A, const
         if (hhi1) off += w1h[kk] * x1h[kk];
         off += wz[kk] * xz[kk];
         if (hz) off += wz[kk + 1] * xz[kk + 2];
-        const T xc = xz[kk + 1];
-        const T d = dd[kk];
-        const T ax = d * xc - A.scale * off;
-        xout[c0 + (long long)kk * nxy] = xc + omega * (bb[kk] - ax) / d;
+        xout[c0 + (long long)kk * nxy] = jacobi_update(xz[kk + 1], bb[kk], dd[kk], A.scale, off, omega);
     }
 }
 
@@ -458,15 +469,14 @@ __global__ void __launch_bounds__(COARSE_BLOCK) k_mg_coarse(const Op<T> A, const
         const T* xin = buf[(s + 1) & 1];
         T* xout = buf[s & 1];
         for (long long c = threadIdx.x; c < A.N; c += COARSE_BLOCK) {
-            const T d = A.diag[c];
+            const T wi = A.wid[c];
             if (s == 0) {
-                xout[c] = omega * b[c] / d;
+                xout[c] = wi * b[c];
             } else {
                 int i, j, k;
                 coords3(A, c, i, j, k);
-                const T xc = xin[c];
-                const T ax = apply_row(A, xin, c, i, j, k, xc);
-                xout[c] = xc + omega * (b[c] - ax) / d;
+                const T off = off_row(A, xin, c, i, j, k);
+                xout[c] = jacobi_update(xin[c], b[c], wi, A.scale, off, omega);
             }
         }
         __syncthreads();
@@ -598,18 +608,32 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_diag_faces(Op<T> A, T* __restr
     }
 }
 
-// FP32 copy of the finest operator with the scale folded into the faces
-__global__ void __launch_bounds__(LIN_BLOCK) k_cast_op(const Op<double> A, float* __restrict__ d,
+// FP32 copy of the finest operator with the scale folded into the faces, and the smoother's
+// omega / diag rounded from FP64
+__global__ void __launch_bounds__(LIN_BLOCK) k_cast_op(const Op<double> A, double omega,
+                                                       float* __restrict__ d,
                                                        float* __restrict__ wx,
                                                        float* __restrict__ wy,
-                                                       float* __restrict__ wz) {
+                                                       float* __restrict__ wz,
+                                                       float* __restrict__ wid) {
     for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < A.N;
          c += (long long)gridDim.x * LIN_BLOCK) {
-        d[c] = (float)A.diag[c];
+        const double dg = A.diag[c];
+        d[c] = (float)dg;
+        wid[c] = (float)(omega / dg);
         wx[c] = (float)(A.scale * A.W[0][c]);
         wy[c] = (float)(A.scale * A.W[1][c]);
         wz[c] = (float)(A.scale * A.W[2][c]);
     }
+}
+
+// wid = omega / diag
+template <typename T>
+__global__ void __launch_bounds__(LIN_BLOCK) k_inv_diag(long long N, const T* __restrict__ diag,
+                                                        T omega, T* __restrict__ wid) {
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+         c += (long long)gridDim.x * LIN_BLOCK)
+        wid[c] = omega / diag[c];
 }
 
 __global__ void __launch_bounds__(LIN_BLOCK) k_to_f32(long long N, const double* __restrict__ a,
@@ -697,7 +721,8 @@ cudaError_t LinLaunch::matvec_ns(const OpNS& A, const double* x, double* y, cons
                                  int two_dots, double* part, int& nparts) {
     nparts = stream_blocks(A.N);
     begin("bicg_matvec");
-    k_matvec_ns<<<nparts, LIN_BLOCK, 0, st>>>(A, x, y, w1, two_dots, part);
+    if (two_dots) k_matvec_ns<true><<<nparts, LIN_BLOCK, 0, st>>>(A, x, y, w1, part);
+    else k_matvec_ns<false><<<nparts, LIN_BLOCK, 0, st>>>(A, x, y, w1, part);
     return end();
 }
 cudaError_t LinLaunch::bicg_init(long long N, const double* b, double* r, double* rh, double* x,
@@ -740,7 +765,8 @@ cudaError_t LinLaunch::smooth(const Op<T>& A, const T* b, const T* xin, T* xout,
     if (A.N == fine_N) begin(sizeof(T) == 4 ? "mg_smooth_f32_fine" : "mg_smooth_f64_fine");
     else begin(sizeof(T) == 4 ? "mg_smooth_f32" : "mg_smooth_f64");
     const long long nxy = (long long)A.nx * A.ny;
-    // (the FP64 instance needs 218 registers and measured slower than the plain sweep)
+    // (FP32 only: the FP64 sweep is bound by its FP64 arithmetic, not by load latency, and
+    // its z-marching form measured slower)
     if (sizeof(T) == 4 && !first && A.nz % ZM == 0 && nxy >= 4 * LIN_BLOCK && xin != xout) {
         const dim3 g((unsigned)((nxy + LIN_BLOCK - 1) / LIN_BLOCK), (unsigned)((A.nz + ZM - 1) / ZM));
         k_mg_smooth_zm<T><<<g, LIN_BLOCK, 0, st>>>(A, b, xin, xout, omega);
@@ -784,9 +810,16 @@ cudaError_t LinLaunch::diag_faces(const Op<T>& A, T* diag) {
     k_mg_diag_faces<T><<<stream_blocks(A.N), LIN_BLOCK, 0, st>>>(A, diag);
     return end();
 }
-cudaError_t LinLaunch::cast_op(const Op<double>& A, float* d, float* wx, float* wy, float* wz) {
+template <typename T>
+cudaError_t LinLaunch::inv_diag(long long N, const T* diag, T omega, T* wid) {
+    begin("mg_inv_diag");
+    k_inv_diag<T><<<stream_blocks(N), LIN_BLOCK, 0, st>>>(N, diag, omega, wid);
+    return end();
+}
+cudaError_t LinLaunch::cast_op(const Op<double>& A, double omega, float* d, float* wx, float* wy,
+                               float* wz, float* wid) {
     begin("mg_cast_op");
-    k_cast_op<<<stream_blocks(A.N), LIN_BLOCK, 0, st>>>(A, d, wx, wy, wz);
+    k_cast_op<<<stream_blocks(A.N), LIN_BLOCK, 0, st>>>(A, omega, d, wx, wy, wz, wid);
     return end();
 }
 cudaError_t LinLaunch::to_f32(long long N, const double* a, float* b) {
@@ -824,5 +857,7 @@ template cudaError_t LinLaunch::coarsen<float, float>(const Op<float>&, int, int
                                                       float*, float*, float*);
 template cudaError_t LinLaunch::diag_faces<double>(const Op<double>&, double*);
 template cudaError_t LinLaunch::diag_faces<float>(const Op<float>&, float*);
+template cudaError_t LinLaunch::inv_diag<double>(long long, const double*, double, double*);
+template cudaError_t LinLaunch::inv_diag<float>(long long, const float*, float, float*);
 
 }  // namespace rhi

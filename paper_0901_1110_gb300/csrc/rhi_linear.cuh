@@ -15,6 +15,7 @@ struct Op {
     const T* diag;
     const T* W[3];       // lower-face coefficient per axis (0 on zero-flux boundary faces)
     T scale;
+    const T* wid;        // omega / diag, read by the multigrid smoothers
 };
 
 // Non-symmetric 7-point operator (the Schur matrix with dD/dE kept):
@@ -98,7 +99,11 @@ struct LinLaunch {
                         TC* wz);
     template <typename T>
     cudaError_t diag_faces(const Op<T>& A, T* diag);
-    cudaError_t cast_op(const Op<double>& A, float* d, float* wx, float* wy, float* wz);
+    // wid = omega / diag, the smoothers' scaled inverse diagonal
+    template <typename T>
+    cudaError_t inv_diag(long long N, const T* diag, T omega, T* wid);
+    cudaError_t cast_op(const Op<double>& A, double omega, float* d, float* wx, float* wy,
+                        float* wz, float* wid);
     cudaError_t to_f32(long long N, const double* a, float* b);
     cudaError_t from_f32_dot(long long N, const float* x, const double* r, double* z,
                              double* part, int& nparts);
