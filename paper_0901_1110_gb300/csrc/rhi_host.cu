@@ -76,6 +76,7 @@ struct Level {
     long long N = 0;
     T* diag = nullptr;
     T* wid = nullptr;           // omega / diag (smoother)
+    T* loc = nullptr;           // diag - sum of the six faces (FP64 restriction; FP32: none)
     T* W[3] = {nullptr, nullptr, nullptr};
     T* b = nullptr;
     T* x = nullptr;
@@ -280,6 +281,7 @@ int mg_build_levels(rhi_ctx* h) {
             }
             if ((rc = dalloc(h, &v.xt, v.N))) return rc;
             if ((rc = dalloc(h, &v.wid, v.N))) return rc;
+            if ((rc = dalloc(h, &v.loc, v.N))) return rc;
         }
     } else if (h->prm.precond == RHI_PRECOND_MG_FP32) {
         h->mg32.resize(nl);
@@ -308,6 +310,7 @@ Op<T> level_op(const rhi_ctx* h, const Level<T>& v) {
     for (int a = 0; a < 3; ++a) { A.per[a] = h->per[a]; A.W[a] = v.W[a]; }
     A.diag = v.diag;
     A.wid = v.wid;
+    A.loc = v.loc;
     A.scale = T(1);
     return A;
 }
@@ -319,17 +322,21 @@ int precond_setup(rhi_ctx* h) {
     if (h->prm.precond == RHI_PRECOND_MG_FP64) {
         auto& lv = h->mg64;
         h->op0.wid = lv[0].wid;
-        CK(L.inv_diag<double>(h->N, h->op0.diag, om, lv[0].wid));
+        h->op0.loc = lv[0].loc;
+        CK((L.level_prep<double, double>(h->op0, om, lv[0].wid, lv[0].loc)));
         for (size_t l = 0; l + 1 < lv.size(); ++l) {
             Op<double> A = (l == 0) ? h->op0 : level_op(h, lv[l]);
             auto& c = lv[l + 1];
             CK((L.coarsen<double, double>(A, c.nx, c.ny, c.nz, c.diag, c.W[0], c.W[1], c.W[2])));
             CK(L.diag_faces<double>(level_op(h, c), c.diag));
-            CK(L.inv_diag<double>(c.N, c.diag, om, c.wid));
+            CK((L.level_prep<double, double>(level_op(h, c), om, c.wid, c.loc)));
         }
     } else if (h->prm.precond == RHI_PRECOND_MG_FP32) {
         auto& lv = h->mg32;
-        CK(L.cast_op(h->op0, om, lv[0].diag, lv[0].W[0], lv[0].W[1], lv[0].W[2], lv[0].wid));
+        CK(L.cast_op(h->op0, lv[0].diag, lv[0].W[0], lv[0].W[1], lv[0].W[2]));
+        // the finest level's omega / diag from the FP64 operator (the FP32 restriction takes
+        // each child's full row and needs no local part)
+        CK((L.level_prep<double, float>(h->op0, om, lv[0].wid, nullptr)));
         for (size_t l = 0; l + 1 < lv.size(); ++l) {
             auto& c = lv[l + 1];
             if (l == 0)
@@ -337,7 +344,7 @@ int precond_setup(rhi_ctx* h) {
             else
                 CK((L.coarsen<float, float>(level_op(h, lv[l]), c.nx, c.ny, c.nz, c.diag, c.W[0], c.W[1], c.W[2])));
             CK(L.diag_faces<float>(level_op(h, c), c.diag));
-            CK(L.inv_diag<float>(c.N, c.diag, (float)om, c.wid));
+            CK((L.level_prep<float, float>(level_op(h, c), om, c.wid, nullptr)));
         }
     }
     return RHI_OK;

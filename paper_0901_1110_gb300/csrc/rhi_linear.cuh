@@ -16,6 +16,7 @@ struct Op {
     const T* W[3];       // lower-face coefficient per axis (0 on zero-flux boundary faces)
     T scale;
     const T* wid;        // omega / diag, read by the multigrid smoothers
+    const T* loc;        // diag - scale * (sum of the six face coefficients); FP64 levels only
 };
 
 // Non-symmetric 7-point operator (the Schur matrix with dD/dE kept):
@@ -99,11 +100,11 @@ struct LinLaunch {
                         TC* wz);
     template <typename T>
     cudaError_t diag_faces(const Op<T>& A, T* diag);
-    // wid = omega / diag, the smoothers' scaled inverse diagonal
-    template <typename T>
-    cudaError_t inv_diag(long long N, const T* diag, T omega, T* wid);
-    cudaError_t cast_op(const Op<double>& A, double omega, float* d, float* wx, float* wy,
-                        float* wz, float* wid);
+    // per cell of a level: wid = omega / diag (smoothers) and, if loc is not null,
+    // loc = diag - scale * (six faces) (FP64 restriction), evaluated in TF and rounded to TO
+    template <typename TF, typename TO>
+    cudaError_t level_prep(const Op<TF>& A, double omega, TO* wid, TO* loc);
+    cudaError_t cast_op(const Op<double>& A, float* d, float* wx, float* wy, float* wz);
     cudaError_t to_f32(long long N, const double* a, float* b);
     cudaError_t from_f32_dot(long long N, const float* x, const double* r, double* z,
                              double* part, int& nparts);
