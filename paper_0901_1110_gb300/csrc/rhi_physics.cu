@@ -55,6 +55,21 @@ cudaError_t launch_kappa(const StepParams& P, int ns, const double* n, double* k
 struct FaceCoef { double W, P, Q, K; };
 
 // JM: 0 W only; 1 W, P, Q (dD/dE kept); 2 W, P, Q, K (exact)
+// The limiter's face coefficients depend on (s, dE) = (a dx Ebar, E_b - E_a) only through
+// their ratio: W, P and Q, and K apart from its factor dE, are homogeneous of degree 0.  Their
+// squares and the 1 / den^2 of the derivatives leave the FP64 range once Ebar falls below about
+// 1e-90 (deep neutral gas after many absorbing steps), and the result turns into 0 / 0 or
+// x * inf.  A faint face is therefore brought to s in [1, 2) by a power of two, which is exact;
+// the test runs on the bit pattern (integer pipe), s > 0 and below 2^-64.
+__device__ __forceinline__ void faint_rescale(double& s, double& dE) {
+    const long long sb = __double_as_longlong(s);
+    if (sb > 0 && sb < 0x3BF0000000000000LL) {
+        const int e = ilogb(s);
+        s = scalbn(s, -e);
+        dE = scalbn(dE, -e);
+    }
+}
+
 template <int JM>
 __device__ __forceinline__ FaceCoef face_coef(const StepParams& P, double Ea, double Eb,
                                               double ka, double kb) {
@@ -64,9 +79,11 @@ __device__ __forceinline__ FaceCoef face_coef(const StepParams& P, double Ea, do
     r.K = 0.0;
     if (P.limiter) {
         const double Esum = Ea + Eb;
-        const double s = Esum * P.half_adx;                     // a dx Ebar
+        double s = Esum * P.half_adx;                           // a dx Ebar
         const double dE = Eb - Ea;
-        const double qraw = fabs(dE);
+        double dEs = dE;                                        // dE on the scale of s
+        faint_rescale(s, dEs);
+        const double qraw = fabs(dEs);
         const double q = fmax(qraw, P.R_min * s);
         const double ks = kap * s;
         const double num = C_LIGHT * s * (2.0 * ks + q);
@@ -85,7 +102,7 @@ __device__ __forceinline__ FaceCoef face_coef(const StepParams& P, double Ea, do
             // R dD/dR (1 -+ t) with t = dE / Esum; s / Esum = a dx / 2, so RdD t needs no division
             const double X = -C_LIGHT * q * q * (4.0 * ks + q) * iden * iden * P.inv_a2dx2;
             const double RdD = X * s;
-            const double RdDt = X * dE * P.half_adx;
+            const double RdDt = X * dEs * P.half_adx;
             r.P = r.W + RdD - RdDt;
             r.Q = r.W + RdD + RdDt;
         } else {
@@ -110,8 +127,9 @@ __device__ __forceinline__ BoundaryFace boundary_face(const StepParams& P, doubl
     BoundaryFace r;
     if (P.limiter) {
         const double Esum = E + Eb;
-        const double s = 0.5 * Esum * P.half_adx;
-        const double dE = Eb - E;
+        double s = 0.5 * Esum * P.half_adx;
+        double dE = Eb - E;
+        faint_rescale(s, dE);
         const double qraw = fabs(dE);
         const double q = fmax(qraw, P.R_min * s);
         const double ks = kap * s;

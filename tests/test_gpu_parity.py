@@ -235,6 +235,29 @@ def test_nonconvergence_leaves_state_unchanged(rhi):
         np.testing.assert_array_equal(before[k], after[k])
 
 
+def test_faint_field_matches_oracle(rhi):
+    """Half of the box starts with a radiation field 1e180 below the rest (E near 1e-200), as
+    deep neutral gas reaches after many absorbing steps.  There the limiter's squares and
+    1 / den^2 leave the FP64 range unless the face is rescaled (0 / 0 at the first residual).
+    The step with the exact Newton matrix must stay finite and positive and match the oracle,
+    which works with R = |dE| / (a dx Ebar) directly."""
+    w = inputs.lognormal_hhe((10, 12, 14), box=200 * KPC, nsrc=2, dt=5e12, nsteps=1, seed=4)
+    w.theta = 1.0
+    w.u_E = 1e-18
+    E = w.E.copy()
+    E[: w.nz // 2] *= 1e-180
+    w.E = E
+    s = rhi.solver_for_workload(w, limiter_jacobian=2)
+    s.step(w.dt, newton_tol=1e-12, lin_tol=1e-12)
+    got = s.get_state()
+    s.close()
+    p = oracle_problem(w)
+    ref, _ = sv.implicit_step(p, w.state(), w.dt, 1.0, 0.0, 1e-13)
+    Eg = np.asarray(got["E"]).reshape(w.nz, w.ny, w.nx)
+    assert np.all(np.isfinite(Eg)) and np.all(Eg > 0)
+    assert max(_field_errors(got, ref).values()) <= TOL_FP64
+
+
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 7), (3, 1, 2)])
 def test_degenerate_grids(rhi, shape):
     """A single cell and line / plane grids (diffusion with fewer than three axes)."""
