@@ -406,3 +406,72 @@ def test_explicit_predictor_is_explicit_euler():
     free = cap == 1.0
     assert free.sum() > p.N // 2
     np.testing.assert_allclose(U0[:, free], (Un - w.dt * L)[:, free], rtol=1e-15)
+
+
+@pytest.mark.parametrize("ns_case", ["h", "hhe"])
+def test_step_caps_is_the_largest_feasible_fraction(ns_case):
+    """The positivity cap (reading of the bounds limiter) is the largest fraction lam <= 1 of the
+    step for which every bounded quantity keeps at least (1 - tau) of its distance to its
+    bound.  Checked per cell by bisection on the stepped state itself: e = e^n + e_c, E and the
+    species, with n_HII, n_HeIII derived from the stepped independent species, so the mapping
+    of a step onto the derived species is pinned as well."""
+    if ns_case == "h":
+        w = inputs.uniform_h(4, shape=(3, 4, 5), box=60 * KPC, dt=3e12, nsteps=1, E0=1e-19)
+    else:
+        w = inputs.lognormal_hhe((3, 4, 5), box=200 * KPC, nsrc=2, dt=5e12, nsteps=1, seed=7)
+    p = oracle_problem(w)
+    st = w.state()
+    U = md.state_to_U(p, st)
+    eh = np.asarray(st["e"], dtype=np.float64).ravel()
+    nH = p.nH.ravel()
+    nHe = p.y_he * nH
+    # cells at the species bounds: fully neutral (n_HII = 0), fully ionised (n_HI = 0), and for
+    # helium n_HeIII = 0, n_HeI = 0, n_HeII = 0
+    k = np.arange(p.N) % 6
+    U[1, k == 0] = nH[k == 0]
+    U[1, k == 1] = 0.0
+    if p.ns == 3:
+        U[3, k == 2] = nHe[k == 2] - U[2, k == 2]
+        U[2, k == 3] = 0.0
+        U[3, k == 4] = 0.0
+    rng = np.random.default_rng(11)
+    # steps of random sign over eight decades of each quantity's scale, so that every bound,
+    # and every pair of species changes of similar size, binds somewhere
+    tot = np.vstack([np.abs(eh)] + [nH] + [nHe] * (p.ns - 1) + [np.abs(U[1 + p.ns])])
+    S = rng.uniform(-1.0, 1.0, size=U.shape) * tot * 10.0 ** rng.uniform(-8.0, 0.5, size=U.shape)
+    cap = sv.step_caps(p, U, eh, S)
+
+    def quantities(V, c):
+        e = eh[c] + V[0]
+        E = V[1 + p.ns]
+        if p.ns == 1:
+            nHI, nHeI, nHeII = V[1], 0.0, 0.0
+        else:
+            nHI, nHeI, nHeII = V[1], V[2], V[3]
+        q = [(e, 0.0), (E, 0.0), (nHI, 1e-13 * nH[c]), (nH[c] - nHI, 1e-13 * nH[c])]
+        if p.ns == 3:
+            q += [(nHeI, 1e-13 * nHe[c]), (nHeII, 1e-13 * nHe[c]),
+                  (nHe[c] - nHeI - nHeII, 1e-13 * nHe[c])]
+        return q
+
+    def feasible(c, lam):
+        before = quantities(U[:, c], c)
+        after = quantities(U[:, c] + lam * S[:, c], c)
+        for (q0, tiny), (q1, _) in zip(before, after):
+            # keep (1 - tau) of the distance q0 + tiny, up to the rounding of the stepped
+            # quantity (a derived species carries that of its element total, 1e13 tiny)
+            slack = 1e-15 * max(abs(q0), abs(q1), 1e13 * tiny)
+            if q1 + tiny < (1.0 - p.tau) * (q0 + tiny) - slack:
+                return False
+        return True
+
+    # a binding derived species near zero has a distance of order tiny, which the rounding
+    # of its element total blurs at the 1e-3 level: the margin on both sides is 5%
+    bound = 0
+    for c in range(p.N):
+        assert 0.0 <= cap[c] <= 1.0
+        assert feasible(c, cap[c] * 0.95)
+        if cap[c] < 1.0:
+            assert not feasible(c, cap[c] * 1.05), (c, cap[c])
+            bound += 1
+    assert bound > 0
