@@ -163,7 +163,7 @@ int rhi_grey_constants(int spectrum, double param, int n_species, double* sk, do
 
 /* Creates a solver for one grid on the current CUDA device.  stream is a cudaStream_t (NULL:
    the legacy default stream).  Allocates every device buffer the step needs.  Errors:
-   RHI_ERR_ARG for non-positive sizes, unpaired periodic faces, n_species not 1 or 3, or
+   RHI_ERR_ARG for non-positive sizes, unpaired periodic faces, n_species not 0, 1 or 3, or
    out-of-range parameters; RHI_ERR_CUDA when allocation fails. */
 int rhi_create(const rhi_grid* grid, const rhi_bc* bc, const rhi_params* params,
                void* stream, rhi_handle* out);
@@ -171,7 +171,9 @@ int rhi_create(const rhi_grid* grid, const rhi_bc* bc, const rhi_params* params,
 /* Sets the state U^n: E (N), e (N, specific gas energy), n (n_species * N), the comoving
    hydrogen density n_H (N) and the emissivity 4 pi eta (N, erg cm^-3 s^-1; NULL = 0).
    Requires E > 0, e > 0, n_H > 0 and every species (independent and derived) >= 0
-   (RHI_ERR_NONPHYSICAL otherwise).  Isothermal runs fix the temperature here. */
+   (RHI_ERR_NONPHYSICAL otherwise).  Isothermal runs fix the temperature here.  The learned
+   guess's retry count (mlp_retry) carries over, so a host that hands its state back every
+   step runs the same steps as one that leaves it on the device. */
 int rhi_set_state(rhi_handle h, const double* E, const double* e, const double* n,
                   const double* n_H, const double* src, int on_device);
 

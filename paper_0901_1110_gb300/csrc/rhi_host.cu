@@ -931,7 +931,6 @@ int rhi_set_state(rhi_handle h, const double* E, const double* e, const double* 
         return fail(h, RHI_ERR_NONPHYSICAL, "rhi_set_state: need E > 0, e > 0, n_H > 0, species >= 0, finite");
     }
     h->have_state = true;
-    h->mlp_skip = 0;
     return RHI_OK;
 }
 
