@@ -1,8 +1,8 @@
 """Benchmark: implicit cell-updates/s of the radiation / ionization / gas-energy step on GB300.
 
 One bench step = one rhi_implicit_step (g^n, Newton iterations with the fused residual /
-Jacobian / Schur kernel, multigrid-preconditioned CG on the Schur system, recovery and
-positivity-limited update) over the 256^3 hydrogen + helium lognormal workload (64 lognormal
+Jacobian / Schur kernel, multigrid-preconditioned Krylov on the Schur system (BiCGStab with the
+exact Newton matrix, the default; CG with D lagged), recovery and positivity-limited update) over the 256^3 hydrogen + helium lognormal workload (64 lognormal
 point sources, T_B = 1e5 K blackbody, 5e12 s steps, Newton tol 1e-8, PCG tol 1e-10).  Three
 forms run on the same workload: plain FP64 (FP64 multigrid), mixed (FP32 multigrid inside
 FP64 CG) and, as the headline, learned + mixed (the mixed form started from the learned
@@ -28,6 +28,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "implicit cell-updates/s at 256^3 (learned+FP32-MG vs plain FP64), HBM GB/s frac"
 UNIT = "cell-updates/s"
+
+
+def max_over_ranks(x, dist, device):
+    """The largest x over the ranks of the process group (x itself without one)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, cells, steps, ms):
+    """Whole-job cell-updates/s of world replicas of `cells` cells each, every rank having
+    taken `steps` steps within the slowest rank's `ms` milliseconds."""
+    return world * cells * steps / (ms * 1e-3)
 
 
 def load_peaks():
@@ -435,18 +451,15 @@ def main():
             limiter_jacobian=args.limiter_jacobian, max_newton=args.max_newton, guess=guess,
             weights=weights if guess == rhi.RHI_GUESS_LEARNED else None)
         clocks = clk.stop()
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        if dist:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        forms[name] = dict(ms=float(t.item()), agg=agg, kt=kt_all, kt_timed=kt_timed,
-                           clocks=clocks)
+        forms[name] = dict(ms=max_over_ranks(ms, dist, "cuda"), agg=agg, kt=kt_all,
+                           kt_timed=kt_timed, clocks=clocks)
         s.close()
         del s
         torch.cuda.empty_cache()
 
     head = forms[order[-1]]
     ms_step = head["ms"] / args.steps
-    value = world * w.N * args.steps / (head["ms"] * 1e-3)
+    value = replica_throughput(world, w.N, args.steps, head["ms"])
 
     # dominant kernel (largest share of the breakdown step) and its roofline from the
     # per-launch device times inside the timed region
@@ -486,7 +499,7 @@ def main():
     lin = hbm_fracs(kt)
 
     def summary(f):
-        return {"value": world * w.N * args.steps / (f["ms"] * 1e-3),
+        return {"value": replica_throughput(world, w.N, args.steps, f["ms"]),
                 "ms_per_step": f["ms"] / args.steps,
                 **{k: v / args.steps for k, v in f["agg"].items()
                    if isinstance(v, (int, float))},
