@@ -144,11 +144,14 @@ typedef struct {
 
 typedef struct rhi_ctx* rhi_handle;
 
-/* Defaults: theta 0.51 (Sec. 3.2), limiter on, tau 0.99, lam_min 1/16, growth_max 1e3,
-   watchdog 3, max_newton 50,
+/* Defaults: theta 0.51 (Sec. 3.2), grey m = 1, limiter on, D lagged in the Newton matrix
+   (limiter_jacobian 0), tau 0.99, lam_min 1/16, growth_max 1e3, watchdog 3, max_newton 50,
    max_pcg 200, previous-step guess, FP64 multigrid with 6 levels, 2 + 2 sweeps, 16 coarse
-   sweeps, omega 0.8, scalings 1, and the grey constants of 13.6 eV monochromatic radiation
-   with a 6.3e-18 cm^2 HI cross section.  n_species must be 1 or 3. */
+   sweeps, omega 0.9, V-cycle graph on, learned-guess gates mlp_gate 1e-3, mlp_ood 6,
+   mlp_restart 12, mlp_retry 4, fixed steps (dt_norm 0) with tau_tol 0.01, scalings 1,
+   kappa_floor 1e-40, mu 0.6, and the grey constants of 13.6 eV monochromatic radiation with a
+   6.3e-18 cm^2 HI cross section.  n_species must be 0 (LTE model), 1 or 3.  Host computation
+   only. */
 int rhi_params_default(rhi_params* p, int n_species);
 
 /* Grey constants of eq. adaptive_spectrum (Sec. 3.2.5) for an assumed spectrum chi(nu):
