@@ -201,6 +201,72 @@ def test_diffusion_step_equals_discrete_exact_solution(bc, theta):
     np.testing.assert_allclose(new["n"], st["n"], rtol=1e-14)
 
 
+def _gaussian_pulse_error(n, nsteps):
+    """Max error, relative to the peak, of theta = 1 steps of a Gaussian pulse in a periodic
+    box (constant kappa, no reactions, limiter off) against the analytic solution."""
+    L, nH = 4.8e22, 1e-3
+    sig0 = L / 8                       # periodic images sit 8 sigma0 away: exp(-16) at the end
+    kap = 6.3e-21 * nH
+    D = cl.C_LIGHT / (3 * kap)
+    T = sig0 ** 2 / (2 * D)            # sigma^2 doubles
+    dt = T / nsteps
+    w = inputs.uniform_h(n, shape=(n, n, n), box=L, x0=0.0, dt=dt, bc=("periodic",) * 6, nH=nH)
+    w.theta = 1.0
+    grey = dict(sk=np.array([6.3e-21, 0, 0]), pgam=np.zeros(3), ph=np.zeros(3))
+    p = oracle_problem(w, grey=grey, limiter=False, src=np.zeros(w.N), u_E=1e-17)
+    st = w.state()
+    x = (np.arange(n) + 0.5) * (L / n) - L / 2
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    r2 = X ** 2 + Y ** 2 + Z ** 2
+    bg, E0 = 1e-20, 1e-17
+    st["E"] = (bg + E0 * np.exp(-r2 / (2 * sig0 ** 2))).ravel()
+    for _ in range(nsteps):
+        st, stats = sv.implicit_step(p, st, dt, 1.0, 0.0, 1e-13, linear="schur_cg")
+        assert stats["converged"]
+    s2 = sig0 ** 2 + 2 * D * T
+    exact = np.exp(-cl.C_LIGHT * kap * T) * (bg + E0 * (sig0 ** 2 / s2) ** 1.5
+                                             * np.exp(-r2 / (2 * s2)))
+    return np.abs(st["E"].reshape(n, n, n) - exact).max() / exact.max()
+
+
+def test_gaussian_pulse_converges_to_the_heat_kernel():
+    """Eqs. radiation_simplified + mDE in the diffusion limit, D = c / (3 kappa), against the
+    analytic solution of dE/dt = D lap E - c kappa E for a Gaussian pulse:
+    E = exp(-c kappa t) (s0^2 / s^2)^(3/2) exp(-r^2 / (2 s^2)), s^2 = s0^2 + 2 D t.
+    With theta = 1 the error is O(dx^2 + dt): halving dx and quartering dt cuts it by about 4."""
+    coarse = _gaussian_pulse_error(24, 8)
+    fine = _gaussian_pulse_error(48, 32)
+    assert fine < 0.025
+    assert 3.3 < coarse / fine < 4.7, (coarse, fine)
+
+
+@pytest.mark.parametrize("limiter", [False, True])
+def test_comoving_grid_is_the_proper_grid(limiter):
+    """Reading of the comoving factors: diffusion (1/a^2) div(D grad E) with R = |grad E| /
+    (a E), opacities from proper densities n / a^3.  A comoving grid of spacing dx at scale
+    factor a (adot = 0) is then the proper grid of spacing a dx holding the proper densities,
+    so one step of the radiation equation (no sources, no photo-absorption by species) gives
+    the same E on both."""
+    shape = (5, 6, 7)
+    nz, ny, nx = shape
+    a = 0.5
+    E0 = 1e-17 * np.exp(np.random.default_rng(3).uniform(-3.0, 3.0, nx * ny * nz))
+    out = []
+    for scale, dx, nH in ((a, 4e21, 1e-3), (1.0, a * 4e21, 1e-3 / a ** 3)):
+        w = inputs.uniform_h(nx, shape=shape, box=nx * dx, x0=0.0, dt=1e9, nH=nH,
+                             bc=("zero_flux",) * 6)
+        w.theta = 1.0
+        grey = dict(sk=np.array([6.3e-21, 0, 0]), pgam=np.zeros(3), ph=np.zeros(3))
+        p = oracle_problem(w, grey=grey, limiter=limiter, src=np.zeros(w.N), u_E=1e-17)
+        st = w.state()
+        st["E"] = E0.copy()
+        new, stats = sv.implicit_step(p, st, w.dt, scale, 0.0, 1e-13, linear="direct")
+        assert stats["converged"]
+        out.append(np.asarray(new["E"]))
+    np.testing.assert_allclose(out[0], out[1], rtol=1e-10, atol=0)
+    assert np.abs(out[0] / E0 - 1).max() > 1e-2          # the step did move E
+
+
 @pytest.mark.parametrize("theta", [1.0, 0.51])
 def test_expansion_terms_closed_form(theta):
     """The cosmological terms -m (adot/a) E (eq. mLE) and -2 (adot/a) e_c (eq. mLe) in a
