@@ -60,3 +60,59 @@ def test_grey_constants_match_oracle_quadrature(rhi, spec, par, ns):
         np.testing.assert_allclose(a[k], b[k], rtol=1e-11, atol=0)
         assert np.all(np.asarray(a[k])[ns:] == 0.0)
     assert abs(a["eps"] / b["eps"] - 1) < 1e-12
+
+
+# ---- argument checks of rhi_create: every one returns before any device call
+
+def _create(rhi, shape=(4, 5, 6), dx=1e21, bc=None, bc_value=(0.0,) * 6, **tweak):
+    p = rhi.rhi_params_default(3)
+    p.y_he = 0.0789
+    for k, v in tweak.items():
+        setattr(p, k, v)
+    kinds = bc if bc is not None else (rhi.RHI_BC_ZERO_FLUX,) * 6
+    return rhi.Solver(*shape, dx, p, bc=kinds, bc_value=bc_value)
+
+
+@pytest.mark.parametrize("shape,dx", [((0, 4, 4), 1e21), ((4, -1, 4), 1e21), ((4, 4, 4), 0.0),
+                                      ((4, 4, 4), float("nan")), ((2048, 2048, 1024), 1e21)])
+def test_create_rejects_bad_grids(rhi, shape, dx):
+    with pytest.raises(rhi.RhiError) as e:
+        _create(rhi, shape=shape, dx=dx)
+    assert e.value.code == rhi.RHI_ERR_ARG
+
+
+def test_create_rejects_bad_boundaries(rhi):
+    Z, P, D = rhi.RHI_BC_ZERO_FLUX, rhi.RHI_BC_PERIODIC, rhi.RHI_BC_DIRICHLET
+    for bc, val in (((P, Z, Z, Z, Z, Z), (0.0,) * 6),            # unpaired periodic
+                    ((Z, Z, 7, Z, Z, Z), (0.0,) * 6),            # unknown kind
+                    ((D, Z, Z, Z, Z, Z), (0.0,) * 6),            # Dirichlet value must be > 0
+                    ((Z, D, Z, Z, Z, Z), (0.0, float("inf"), 0, 0, 0, 0))):
+        with pytest.raises(rhi.RhiError) as e:
+            _create(rhi, bc=bc, bc_value=val)
+        assert e.value.code == rhi.RHI_ERR_ARG, bc
+
+
+@pytest.mark.parametrize("tweak", [
+    dict(n_species=2), dict(theta=0.0), dict(theta=1.5), dict(u_E=0.0), dict(tau=1.0),
+    dict(lam_min=0.0), dict(growth_max=0.5), dict(watchdog=-1), dict(max_pcg=0),
+    dict(guess=9), dict(mlp_gate=-1.0), dict(mlp_retry=-1), dict(precond=7), dict(mg_levels=0),
+    dict(mg_pre=0), dict(mg_coarse_sweeps=0), dict(limiter_jacobian=3), dict(mg_omega=1.5),
+    dict(vcycle_graph=2), dict(dt_norm=-2), dict(dt_tau_tol=0.0), dict(y_he=-0.1),
+    dict(model=1)])                                   # the LTE model needs n_species = 0
+def test_create_rejects_out_of_range_parameters(rhi, tweak):
+    with pytest.raises(rhi.RhiError) as e:
+        _create(rhi, **tweak)
+    assert e.value.code == rhi.RHI_ERR_ARG
+
+
+def test_null_handles_and_status_strings(rhi):
+    lib = rhi.lib()
+    assert lib.rhi_set_state(None, None, None, None, None, None, 0) == rhi.RHI_ERR_ARG
+    assert lib.rhi_implicit_step(None, 1.0, 1.0, 0.0, 1e-8, 1e-10) == rhi.RHI_ERR_ARG
+    assert lib.rhi_get_state(None, None, None, None, 0) == rhi.RHI_ERR_ARG
+    assert lib.rhi_get_stats(None, None) == rhi.RHI_ERR_ARG
+    assert lib.rhi_last_error(None) == b"null handle"
+    texts = {lib.rhi_status_string(c) for c in (rhi.RHI_OK, rhi.RHI_ERR_ARG, rhi.RHI_ERR_CUDA,
+                                                rhi.RHI_ERR_NONCONVERGED,
+                                                rhi.RHI_ERR_NONPHYSICAL, rhi.RHI_ERR_STATE)}
+    assert len(texts) == 6 and lib.rhi_status_string(99) == b"unknown status"
