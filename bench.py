@@ -367,12 +367,24 @@ def e2e_form(rhi, w, torch, steps, warmup, precond, limiter_jacobian=0, max_newt
         s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol)
     s.get_state(E, e, n)
     torch.cuda.synchronize()
+    # each call returns after its stream work is done, so the wall clock between calls splits
+    # the step into copies in, the solve and copies out
+    split = dict(set_state=0.0, set_sources=0.0, step=0.0, get_state=0.0)
     t0 = time.perf_counter()
     for _ in range(steps):
+        ta = time.perf_counter()
         s.set_state(E, e, n, nH, None)
+        tb = time.perf_counter()
         s.set_sources(w.src_ijk, w.src_rate)
+        tc = time.perf_counter()
         s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol)
+        td = time.perf_counter()
         s.get_state(oE, oe, on)
+        te = time.perf_counter()
+        split["set_state"] += tb - ta
+        split["set_sources"] += tc - tb
+        split["step"] += td - tc
+        split["get_state"] += te - td
         E, oE = oE, E
         e, oe = oe, e
         n, on = on, n
@@ -381,7 +393,7 @@ def e2e_form(rhi, w, torch, steps, warmup, precond, limiter_jacobian=0, max_newt
     s.close()
     h2d = 8 * N * (3 + w.ns) + 20 * len(w.src_rate)
     d2h = 8 * N * (2 + w.ns)
-    return N * steps / dt, h2d, d2h
+    return N * steps / dt, h2d, d2h, {k: 1e3 * v / steps for k, v in split.items()}
 
 
 def main():
@@ -534,11 +546,11 @@ def main():
     if rank == 0:
         if not args.no_e2e:
             pc, guess = FORMS[order[-1]]
-            e2e_val, h2d, d2h = e2e_form(rhi, w, torch, args.steps, args.warmup, pc,
-                                         args.limiter_jacobian, args.max_newton, guess,
-                                         weights if guess == rhi.RHI_GUESS_LEARNED else None)
+            e2e_val, h2d, d2h, split = e2e_form(rhi, w, torch, args.steps, args.warmup, pc,
+                                                args.limiter_jacobian, args.max_newton, guess,
+                                                weights if guess == rhi.RHI_GUESS_LEARNED else None)
             line["e2e"] = {"value": world * e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                           "d2h_bytes_per_step": d2h}
+                           "d2h_bytes_per_step": d2h, "wall_ms_per_step": split}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_sample()
         print(json.dumps(line), flush=True)
