@@ -30,6 +30,18 @@ METRIC = "implicit cell-updates/s at 256^3 (learned+FP32-MG vs plain FP64), HBM 
 UNIT = "cell-updates/s"
 
 
+def workload_sources(n):
+    """Point sources of the n^3 lognormal workload: 64 at 256^3, the same density otherwise."""
+    return max(1, round(64 * (n / 256) ** 3))
+
+
+def workload_text(n):
+    """The timed workload as the JSON line names it (both arms)."""
+    return (f"lognormal_hhe {n}^3 H+He, sigma_ln=1, P(k)~k^-2, {workload_sources(n)} sources "
+            "(median 1e49/s), T_B=1e5 K, dt=5e12 s, theta=1, Newton tol 1e-8 (u_E = 1e-16), "
+            "Krylov tol 1e-10 relative to ||f||")
+
+
 def max_over_ranks(x, dist, device):
     """The largest x over the ranks of the process group (x itself without one)."""
     if dist is None:
@@ -209,8 +221,9 @@ def reference_arm(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"lognormal_hhe {n}^3 sub-box of the 256^3 recipe",
-                       "form": "oracle (numpy/scipy FP64, Schur + plain CG)"},
+            "config": {"workload": workload_text(args.n),
+                       "form": "oracle (numpy/scipy FP64, Schur + plain CG), each step on a "
+                               f"{n}^3 sub-box of that workload"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                              "sample": f"{args.steps} implicit steps of a {n}^3 sub-box "
                                        "(same generator, 1 Mpc/256 cells)"},
@@ -437,7 +450,7 @@ def main():
     from paper_0901_1110_gb300 import inputs
 
     n = args.n
-    nsrc = max(1, round(64 * (n / 256) ** 3))
+    nsrc = workload_sources(n)
     w = inputs.config_lognormal(n, nsrc=nsrc, seed=rank)
     hbm_peak, peak_src = load_peaks()
 
@@ -523,9 +536,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"lognormal_hhe {n}^3 H+He, sigma_ln=1, P(k)~k^-2, {nsrc} sources "
-                               "(median 1e49/s), T_B=1e5 K, dt=5e12 s, theta=1, Newton tol "
-                               "1e-8 (u_E = 1e-16), Krylov tol 1e-10 relative to ||f||",
+        "config": {"workload": workload_text(n),
                    "form": FORM_TEXT[order[-1]],
                    "newton_matrix": NEWTON_TEXT[args.limiter_jacobian],
                    "parallelism": "replicas" if world > 1 else "1 GPU",
