@@ -293,7 +293,9 @@ int rhi_mlp_train(rhi_handle h, const float* X, const float* Y, long long n, int
    RHI_NOALLOC_MAX_COUNT is rejected with RHI_ERR_ARG before any launch.  The first call on a
    device looks up the scratch address for that device (make it before any stream capture).
    Every call overwrites the whole scratch it uses and nothing in it needs to start at zero,
-   but calls that overlap on the GPU (different streams or host threads) race on it. */
+   but calls that overlap on the GPU (different streams or host threads) race on it.  The call
+   clears a launch error still pending from earlier work of the calling host thread
+   (cudaGetLastError) before it launches, and reports RHI_ERR_CUDA only for its own launches. */
 #define RHI_NOALLOC_MAX_COUNT 33554432LL
 int rhi_rms_norm_noalloc(const double* v, long long n, long long count, double* out,
                          void* stream);

@@ -15,7 +15,7 @@ namespace {
 constexpr int NA_BLOCK = 256;
 constexpr long long NA_MAX_PARTIALS = RHI_NOALLOC_MAX_COUNT / NA_BLOCK;
 
-// one partial sum per block of the first kernel, and the final result
+// one partial sum per block of the first kernel (the result goes to the caller's `out`)
 static __device__ __align__(256) double na_scratch[NA_MAX_PARTIALS];
 
 __global__ void __launch_bounds__(NA_BLOCK) k_na_partials(const double* __restrict__ v, long long n,
@@ -60,7 +60,12 @@ extern "C" int rhi_rms_norm_noalloc(const double* v, long long n, long long coun
     }
     const cudaStream_t st = (cudaStream_t)stream;
     const long long nb = (n + NA_BLOCK - 1) / NA_BLOCK;      // <= NA_MAX_PARTIALS
+    // a launch error left pending by earlier work of this host thread is cleared here, so that
+    // each launch below is judged on its own status
+    (void)cudaGetLastError();
     k_na_partials<<<(unsigned)nb, NA_BLOCK, 0, st>>>(v, n, part);
+    if (cudaGetLastError() != cudaSuccess) return RHI_ERR_CUDA;
     k_na_finish<<<1, NA_RED, 0, st>>>(part, (int)nb, 1.0 / (double)count, out);
-    return cudaGetLastError() == cudaSuccess ? RHI_OK : RHI_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return RHI_ERR_CUDA;
+    return RHI_OK;
 }
