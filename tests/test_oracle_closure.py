@@ -180,3 +180,96 @@ def test_source_deposit_conserves_photon_energy_rate():
     src = cl.deposit_sources((4, 5, 6), 2.0, ijk, rate, 3.0)
     assert abs(src.sum() * 8.0 - rate.sum() * 3.0) < 1e-12 * rate.sum() * 3.0
     assert src[3, 2, 1] == 3e48 * 3.0 / 8.0
+
+
+# ---- the terms of the closure whose constants no printed value fixes: pins from physics that
+# the code does not contain (fundamental constants, transition energies, detailed balance of
+# collisional excitation)
+
+# CGS fundamental constants used only by these pins
+E_CHARGE = 4.80320471e-10        # esu
+M_E = 9.1093837015e-28           # g
+
+
+def test_bremsstrahlung_prefactor_from_fundamental_constants():
+    """Free-free emission of a thermal plasma (Rybicki & Lightman 1979, eq. 5.15b):
+    eps_ff = (2^5 pi e^6 / (3 h m_e c^3)) (2 pi k T / (3 m_e))^(1/2) Z^2 n_e n_i g_B.  The
+    closure's amplitude divided by its Gaunt factor and sqrt(T) equals that prefactor (1.4256e-27
+    cgs) to the three figures the fit quotes."""
+    pref = (2 ** 5 * math.pi * E_CHARGE ** 6 / (3 * cl.H_PLANCK * M_E * cl.C_LIGHT ** 3)
+            * math.sqrt(2 * math.pi * cl.K_BOLTZ / (3 * M_E)))
+    T = np.logspace(3, 8, 11)
+    t = cl.closure_terms(T)
+    amp = t["brem"] / (np.sqrt(T) * cl._gaunt(T))
+    np.testing.assert_allclose(amp, pref, rtol=5e-3)
+
+
+def test_bremsstrahlung_gaunt_factor_in_its_physical_range():
+    """The frequency-averaged free-free Gaunt factor lies between 1.1 and 1.5 (Rybicki &
+    Lightman 1979, Sec. 5.2); the fit peaks at log10 T = 5.5."""
+    T = np.logspace(2, 9, 71)
+    g = cl._gaunt(T)
+    assert np.all((g >= 1.1) & (g <= 1.5))
+    assert abs(np.log10(T[np.argmax(g)]) - 5.5) < 0.05
+
+
+def test_collisional_excitation_thresholds_are_the_lyman_alpha_energies():
+    """Collisional excitation of HI and HeII cools through the n = 1 -> 2 transition of a
+    hydrogen-like ion, 3/4 of its ionisation energy (10.2 eV and 40.8 eV): the temperature in
+    the Boltzmann factor of each fit, recovered from the fit at T and 2T with the fit's other
+    T-dependence divided out, is that energy over k_B."""
+    T = np.array([2e4, 1e5, 4e5])
+    d5 = lambda x: 1.0 + np.sqrt(x / 1e5)
+    for key, chi, pw in (("cool_ce_HI", 13.6, 0.0), ("cool_ce_HeII", 54.4, -0.397)):
+        t1 = cl.closure_terms(T)[key]
+        t2 = cl.closure_terms(2 * T)[key]
+        boltz_ratio = (t2 / t1) * (d5(2 * T) / d5(T)) / 2.0 ** pw
+        T_exp = np.log(boltz_ratio) / (1.0 / T - 1.0 / (2 * T))
+        np.testing.assert_allclose(T_exp, 0.75 * chi * cl.EV / cl.K_BOLTZ, rtol=1e-3)
+
+
+def _collision_strength(cool, T, dE, g1=2.0):
+    """Effective collision strength of a collisional-excitation cooling coefficient
+    cool = dE q12 with q12 = 8.629e-6 Omega / (g1 sqrt(T)) exp(-dE / kT) cm^3/s (detailed
+    balance of collisional excitation, Osterbrock & Ferland 2006, Sec. 3.5)."""
+    return cool * np.sqrt(T) * g1 / (8.629e-6 * dE * np.exp(-dE / (cl.K_BOLTZ * T)))
+
+
+def test_collisional_excitation_amplitudes_give_physical_collision_strengths():
+    """The HI and HeII excitation cooling fits correspond to effective collision strengths of
+    order one for HI (0.3..3 over 5e3..1e5 K) and about 1/Z^2 of that for HeII; hydrogenic
+    scaling Z^2 Omega_HeII(Z^2 T) ~ Omega_HI(T) holds within the spread of the fits.  A slip
+    of a decade in either amplitude fails."""
+    T = np.array([5e3, 1e4, 2e4, 5e4, 1e5])
+    dH, dHe = 0.75 * 13.6 * cl.EV, 0.75 * 54.4 * cl.EV
+    oH = _collision_strength(cl.closure_terms(T)["cool_ce_HI"], T, dH)
+    oHe = _collision_strength(cl.closure_terms(4 * T)["cool_ce_HeII"], 4 * T, dHe)
+    assert np.all((oH > 0.3) & (oH < 3.0)), oH
+    assert np.all((oHe > 0.1) & (oHe < 1.0)), oHe
+    r = 4.0 * oHe / oH
+    assert np.all((r > 0.4) & (r < 2.5)), r
+
+
+def test_dielectronic_recombination_cools_by_the_core_transition_energy():
+    """Dielectronic recombination of HeII proceeds through the 1s -> 2p excitation of the core
+    (40.8 eV): each recombination carries that energy away (the cooling fit over the rate fit),
+    and the Boltzmann factor of the resonance uses it (exponent temperature within 1%)."""
+    T = np.logspace(4, 7, 7)
+    t = cl.closure_terms(T)
+    per = t["cool_di_HeII"] / t["alpha_HeII_di"] / cl.EV
+    np.testing.assert_allclose(per, 40.8, rtol=5e-3)
+    dE = 0.75 * 54.4 * cl.EV
+    # d ln(alpha T^1.5) / d(1/T) = -T0 (1 + small second resonance term)
+    Tb = np.array([3e4, 4e4])
+    a = cl.closure_terms(Tb)["alpha_HeII_di"] * Tb ** 1.5
+    T0 = -np.log(a[1] / a[0]) / (1.0 / Tb[1] - 1.0 / Tb[0])
+    assert abs(T0 / (dE / cl.K_BOLTZ) - 1.0) < 1e-2, T0
+
+
+def test_helium_case_b_recombination_close_to_hydrogen_at_nebular_temperatures():
+    """Case-B recombination of He+ to He0 and of H+ to H0 have nearly equal coefficients at
+    5e3..2e4 K (both ~2.6e-13 cm^3/s at 1e4 K; Osterbrock & Ferland 2006, Tables 2.1 and 2.4):
+    the HeII fit lies within 10% of the hydrogen fit there."""
+    T = np.array([5e3, 1e4, 2e4])
+    t = cl.closure_terms(T)
+    np.testing.assert_allclose(t["alpha_HeII_B"] / t["alpha_HII_B"], 1.0, rtol=0.1)
