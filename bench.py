@@ -77,59 +77,74 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 ALU_FLOPS = {
     "cell_residual_schur": 532,
 }
-# DRAM bytes per launch (read + write) from ncu, per cell of a 128^3 capture times the cells
-# of the timed grid (the kernel streams every field once, so traffic grows with the cells);
+# DRAM bytes per launch (read + write) from ncu, per cell of a capture times the cells of the
+# timed grid (each of these kernels streams its fields once, so traffic grows with the cells);
 # an entry is removed when its kernel changes.  The cell kernel's entry (521.9e6 / 128^3) went
-# with the exact rescaling of faint limiter faces, which touched its Dirichlet-face code; the
-# roofline's traffic is null until the kernel is captured again.
+# with the exact rescaling of faint limiter faces, which touched its Dirichlet-face code.
 TRAFFIC_PER_CELL = {}
-# launches bracketed by events inside the timed region
-# (the FP32 V-cycle replays as one CUDA graph, so its kernels are not bracketed one by one)
-TIMED_KERNELS = ["cell_residual_schur"]
 
 FORM_TEXT = {
-    "plain_fp64": "FP64 Newton/Schur/Krylov + FP64 multigrid V-cycle (6 levels, 2+2 Jacobi, "
-                  "16 coarse sweeps), Newton from U^n",
-    "mixed_fp32mg": "FP64 Newton/Schur/Krylov + FP32 multigrid V-cycle (6 levels, 2+2 Jacobi, "
-                    "16 coarse sweeps), Newton from U^n",
-    "learned_mixed": "mixed form + learned Newton guess (BF16 tensor-core MLP 9-64-64-64-6, "
-                     "falls back to U^n when its ||f|| is larger)",
+    "plain_fp64": "FP64 Newton/Schur/BiCGStab + FP64 multigrid V-cycle of the Newton matrix "
+                  "(6 levels, 2+2 Jacobi, 16 coarse sweeps), Newton from U^n",
+    "mixed_fp32mg": "FP64 Newton/Schur/BiCGStab + FP32 multigrid V-cycle of the Newton matrix "
+                    "(6 levels, 2+2 Jacobi, 16 coarse sweeps), Newton from U^n",
+    "learned_mixed": "mixed form + learned Newton guess (BF16 tensor-core MLP, falls back to U^n "
+                     "when its ||f|| is larger)",
 }
 NEWTON_TEXT = {0: "Newton matrix with D lagged (symmetric Schur matrix, CG)",
                1: "Newton matrix with dD/dE kept (BiCGStab)",
                2: "exact Newton matrix: dD/dE and D's opacity dependence kept (BiCGStab)"}
 
-# algorithmic DRAM bytes per cell of each kernel (H + He; FP64 fields 8 B): the fields each
-# launch must read and write once; stencil neighbours come from cache
-ALG_BYTES = {
-    "cell_residual_schur": 8 * (5 + 5 + 3 + 3 + 1) + 8 * (1 + 1 + 4 + 4),
-    "cell_prep_residual_schur": 8 * (4 + 1 + 3 + 3) + 8 * (5 + 1 + 1 + 4 + 4),
-    "faces_limiter": 8 * 2 + 8 * 3,
-    "update_recover_limit": 8 * (5 + 1 + 1 + 1 + 4 + 4) + 8 * (5 + 1),
-    "cg_matvec_dot": 8 * (1 + 3 + 1) + 8,
-    "cg_update_xr": 8 * 4 + 8 * 2,
-    "cg_update_p": 8 * 2 + 8,
-    # BiCGStab (exact Newton matrix): y = A x reads x, diag, P and Q of 3 faces, the dot's
-    # vector; writes y
-    "bicg_matvec": 8 * (1 + 1 + 3 + 3 + 1) + 8,
-    "bicg_update_xr": 8 * 6 + 8 * 2,
-    "bicg_update_p": 8 * 3 + 8,
-    "bicg_update_s": 8 * 2 + 8,
-    "kappa": 8 * 3 + 8,
-    # weighted-Jacobi sweep on the finest level: x, b, omega / diag, 3 lower faces read, x
-    # written; the first sweep of a cycle starts from x = 0 and reads b and omega / diag
-    # only: the 1 + 3 sweeps of a 2 + 2 cycle average
-    "mg_smooth_f32_fine": (4 * 3 + 3 * 4 * 7) / 4,
-    "mg_smooth_f64_fine": (8 * 3 + 3 * 8 * 7) / 4,
-    # FP64 Krylov vector to the FP32 right-hand side, and back with the dot r.z
-    "mg_to_f32": 8 + 4,
-    "mg_from_f32_dot": 4 + 8 + 8,
-}
+
+def alg_bytes(nonsym):
+    """Algorithmic DRAM bytes per cell of each kernel (H + He; FP64 fields 8 B, FP32 4 B): the
+    fields each launch must read and write once; stencil neighbours come from cache.  nonsym:
+    the multigrid levels carry both couplings of each face (the Newton matrix that keeps
+    dD/dE), 6 face arrays instead of 3."""
+    f = 6 if nonsym else 3
+    return {
+        "cell_residual_schur": 8 * (5 + 5 + 3 + 3 + 1) + 8 * (1 + 1 + 4 + 4),
+        "cell_prep_residual_schur": 8 * (4 + 1 + 3 + 3) + 8 * (5 + 1 + 1 + 4 + 4),
+        "faces_limiter": 8 * 2 + 8 * 3,
+        "update_recover_limit": 8 * (5 + 1 + 1 + 1 + 4 + 4) + 8 * (5 + 1),
+        "cg_matvec_dot": 8 * (1 + 3 + 1) + 8,
+        "cg_update_xr": 8 * 4 + 8 * 2,
+        "cg_update_p": 8 * 2 + 8,
+        # BiCGStab (exact Newton matrix): y = A x reads x, diag, P and Q of 3 faces, the dot's
+        # vector; writes y
+        "bicg_matvec": 8 * (1 + 1 + 3 + 3 + 1) + 8,
+        "bicg_update_xr": 8 * 6 + 8 * 2,
+        "bicg_update_p": 8 * 3 + 8,
+        "bicg_update_s": 8 * 2 + 8,
+        "kappa": 8 * 3 + 8,
+        # weighted-Jacobi sweep on the finest level: x, b, omega / diag and the face arrays
+        # read, x written; the first sweep of a cycle starts from x = 0: b, omega / diag read
+        "mg_smooth_f32_fine": 4 * (3 + f) + 4,
+        "mg_smooth_f32_fine_first": 4 * 2 + 4,
+        "mg_smooth_f64_fine": 8 * (3 + f) + 8,
+        "mg_smooth_f64_fine_first": 8 * 2 + 8,
+        # residual restriction from the finest level: b, x, diag and the face arrays of each
+        # fine cell read, one coarse value per 8 fine cells written
+        "mg_restrict_f32_fine": 4 * (3 + f) + 4 / 8,
+        "mg_restrict_f64_fine": 8 * (3 + f) + 8 / 8,
+        # prolongation to the finest level: the parent's correction (one per 8 cells) read, x
+        # read and written
+        "mg_prolong_f32_fine": 4 / 8 + 4 + 4,
+        "mg_prolong_f64_fine": 8 / 8 + 8 + 8,
+        # FP64 Krylov vector to the FP32 right-hand side, and the FP32 result back to FP64
+        "mg_to_f32": 8 + 4,
+        "mg_from_f32": 4 + 8,
+        "mg_from_f32_dot": 4 + 8 + 8,
+    }
+
+
 # the stencil / vector kernels of the Krylov solver and the multigrid preconditioner whose HBM
 # fraction is reported per form
 LINEAR_KERNELS = ("cg_matvec_dot", "cg_update_xr", "cg_update_p", "bicg_matvec",
                   "bicg_update_xr", "bicg_update_p", "bicg_update_s", "mg_smooth_f32_fine",
-                  "mg_smooth_f64_fine", "mg_to_f32", "mg_from_f32_dot")
+                  "mg_smooth_f32_fine_first", "mg_smooth_f64_fine", "mg_smooth_f64_fine_first",
+                  "mg_restrict_f32_fine", "mg_restrict_f64_fine", "mg_prolong_f32_fine",
+                  "mg_prolong_f64_fine", "mg_to_f32", "mg_from_f32", "mg_from_f32_dot")
 
 
 class ClockSampler:
@@ -188,7 +203,7 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
-def _oracle_subbox(n, nsrc):
+def _oracle_subbox(n, nsrc, **overrides):
     """A sub-box of the 256^3 recipe (same generator, same cell size) as an oracle problem."""
     from paper_0901_1110_gb300 import inputs
     from oracle import closure as cl, model as md
@@ -196,7 +211,7 @@ def _oracle_subbox(n, nsrc):
     grey = cl.grey_constants(*w.spectrum, w.ns)
     p = md.Problem(nx=n, ny=n, nz=n, dx=w.dx, ns=w.ns, nH=w.nH, grey=grey, y_he=w.y_he,
                    src=cl.deposit_sources(w.nH.shape, w.dx, w.src_ijk, w.src_rate, grey["eps"]),
-                   theta=w.theta, u_e=w.u_e, u_n=w.u_n, u_E=w.u_E)
+                   theta=w.theta, u_e=w.u_e, u_n=w.u_n, u_E=w.u_E, **overrides)
     return w, p
 
 
@@ -239,45 +254,116 @@ def host_cores():
         return os.cpu_count()
 
 
-def cpu_baseline_sample():
-    """Oracle on a bounded sample: 3 implicit steps of a 48^3 sub-box (same recipe)."""
+def cpu_baseline_sample(n=48, steps=3):
+    """Oracle on a bounded sample: 3 implicit steps of a 48^3 sub-box (same recipe), timed.
+    Untimed afterwards, the oracle's states of the same steps converged to 1e-14 (exact
+    Newton matrix, Schur complement and BiCGStab to 1e-14), against which the GPU forms'
+    per-element errors are reported."""
     from oracle import solve as sv
-    n, steps = 48, 3
     w, p = _oracle_subbox(n, 1)
     st = w.state()
     t0 = time.perf_counter()
     for _ in range(steps):
         st, _ = sv.implicit_step(p, st, w.dt, 1.0, 0.0, w.newton_tol, linear="schur_cg")
     dt = time.perf_counter() - t0
-    return {"value": w.N * steps / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+    base = {"value": w.N * steps / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
             "sample": f"{steps} implicit steps of a {n}^3 sub-box of the 256^3 recipe "
                       "(numpy/scipy; BLAS threads over the host cores)"}
+    _, pe = _oracle_subbox(n, 1, limiter_jacobian="exact")
+    ref, refs = w.state(), []
+    for _ in range(steps):
+        ref, _ = sv.implicit_step(pe, ref, w.dt, 1.0, 0.0, 1e-14, linear="schur_cg")
+        refs.append(ref)
+    return base, (w, refs)
 
 
-def run_form(rhi, w, torch, steps, warmup, precond, time_names, limiter_jacobian=0,
-             max_newton=200, guess=0, weights=None):
+def _per_element(got, ref, nH, y_he):
+    """max over cells of |got - ref| / (|ref| + 1e-12 max|ref|) for E, e and the species
+    fractions x_HI, x_HII, x_HeI, x_HeII, x_HeIII."""
+    def rel(a, b, ulps=0.0):
+        a, b = np.asarray(a).ravel(), np.asarray(b).ravel()
+        d = np.maximum(np.abs(a - b) - ulps * 2.0 ** -52, 0.0)
+        return float((d / (np.abs(b) + 1e-12 * np.abs(b).max())).max())
+
+    def fr(n):
+        n = np.asarray(n).reshape(3, -1)
+        nHe = y_he * nH
+        return {"x_HI": n[0] / nH, "x_HII": (nH - n[0]) / nH, "x_HeI": n[1] / nHe,
+                "x_HeII": n[2] / nHe, "x_HeIII": (nHe - n[1] - n[2]) / nHe}
+
+    out = {"E": rel(got["E"], ref["E"]), "e": rel(got["e"], ref["e"])}
+    fg, fo = fr(got["n"]), fr(ref["n"])
+    # derived fractions (formed by subtraction from the element total) net of 4 units of 2^-52
+    out.update({k: rel(fg[k], fo[k], 4.0 if k in ("x_HII", "x_HeIII") else 0.0) for k in fo})
+    return out
+
+
+def error_vs_oracle(rhi, forms, w, refs, limiter_jacobian, weights):
+    """Per-element error of each GPU form after each of the oracle's steps of the sub-box, run
+    with the timed run's settings (tolerances, Newton matrix, 6 multigrid levels); the worst
+    over the steps per field."""
+    out = {}
+    nH = w.nH.ravel()
+    for name, (pc, guess) in forms.items():
+        s = rhi.solver_for_workload(w, precond=pc, mg_levels=6, theta=1.0,
+                                    limiter_jacobian=limiter_jacobian, max_newton=200,
+                                    guess=guess)
+        if guess == rhi.RHI_GUESS_LEARNED:
+            s.mlp_set_weights(weights)
+        worst, scaled = {}, {}
+        for ref in refs:
+            s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol)
+            got = s.get_state()
+            for k, v in _per_element(got, ref, nH, w.y_he).items():
+                worst[k] = max(worst.get(k, 0.0), v)
+            # distance in the scaled unknowns whose RMS residual Newton stops on
+            for k, u in (("E", w.u_E), ("e", w.u_e)):
+                v = float(np.abs(np.asarray(got[k]).ravel() - np.asarray(ref[k]).ravel()).max() / u)
+                scaled[k] = max(scaled.get(k, 0.0), v)
+            v = float(np.abs(np.asarray(got["n"]).reshape(3, -1)
+                             - np.asarray(ref["n"]).reshape(3, -1)).max() / w.u_n)
+            scaled["n"] = max(scaled.get("n", 0.0), v)
+        s.close()
+        out[name] = {"per_element": worst, "scaled": scaled}
+    return out
+
+
+def dominant_kernel(kt, ab):
+    """The kernel with the largest share of the profiled step among those with a byte or flop
+    model (graph wrappers excluded)."""
+    cands = {k: v for k, v in kt.items() if k in ab or k in ALU_FLOPS}
+    return max(cands.items(), key=lambda kv: kv[1][0])[0] if cands else None
+
+
+def run_form(rhi, w, torch, steps, warmup, precond, ab, limiter_jacobian=0, max_newton=200,
+             guess=0, weights=None):
     """Times `steps` implicit steps after `warmup` with CUDA events on the library's stream.
-    Inside the timed region only the launches named in `time_names` are bracketed by events
-    (their per-launch device time gives the roofline); one further step after the timed
-    region brackets every launch for the per-kernel breakdown."""
+    The last warm-up step brackets every launch with events (the per-kernel breakdown; the
+    Krylov solve then runs as direct launches); it names the dominant kernel, and inside the
+    timed region only that kernel's launches are bracketed (their mean device time gives the
+    roofline).  The Krylov solve runs as a CUDA graph unless that kernel is one of its own."""
     stream = torch.cuda.Stream()
     s = rhi.solver_for_workload(w, stream=stream.cuda_stream, precond=precond, mg_levels=6,
                                 theta=1.0, limiter_jacobian=limiter_jacobian,
                                 max_newton=max_newton, guess=guess)
     if weights is not None:
         s.mlp_set_weights(weights)
-    for _ in range(warmup):
+    for k in range(warmup):
+        if k == warmup - 1:
+            s.set_profiling(True)
         rc = s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol, check=False)
         if rc:
             st = s.stats()
             raise RuntimeError(f"warm-up step failed ({rc}): newton_its={st['newton_its']} "
                                f"residuals={st['res_history']}")
-    s.set_profiling(True, names=time_names)
+    kt_all = s.kernel_times()
+    tname = dominant_kernel(kt_all, ab)
+    s.set_profiling(True, names=[tname] if tname else None)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     agg = dict(newton_its=0, pcg_its=0, vcycles=0, launches=0, backtracks=0, learned_used=0,
-               guess_restarts=0)
+               guess_restarts=0, host_syncs=0, krylov_fallbacks=0)
     e0.record(stream)
     hist, res0, prev0 = [], [], []
     for _ in range(steps):
@@ -294,15 +380,44 @@ def run_form(rhi, w, torch, steps, warmup, precond, time_names, limiter_jacobian
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     kt_timed = s.kernel_times()
+    s.set_profiling(False)
     agg["res_history_last"] = hist[-1]
     agg["res_initial"] = res0
     agg["res_prev_guess"] = prev0
-    # per-kernel breakdown of one more step, every launch bracketed (not part of the timing)
-    s.set_profiling(True)
-    s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol)
-    kt_all = s.kernel_times()
-    s.set_profiling(False)
-    return s, ms, agg, kt_timed, kt_all
+    return s, ms, agg, kt_timed, kt_all, tname
+
+
+def config_128_plain(rhi, torch, limiter_jacobian, max_newton):
+    """The 128^3 plain FP64 configuration as specified: H + He lognormal medium, 16 sources,
+    20 steps of 5e12 s from the initial state, FP64 multigrid; device time of the 20 steps and
+    the Newton and Krylov counts per step."""
+    from paper_0901_1110_gb300 import inputs
+    w = inputs.config_lognormal(128, nsrc=16, seed=0)
+    stream = torch.cuda.Stream()
+    s = rhi.solver_for_workload(w, stream=stream.cuda_stream, precond=rhi.RHI_PRECOND_MG_FP64,
+                                mg_levels=6, theta=1.0, limiter_jacobian=limiter_jacobian,
+                                max_newton=max_newton)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    its = []
+    for _ in range(w.nsteps):
+        s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol)
+        st = s.stats()
+        its.append((st["newton_its"], st["pcg_its"], st["vcycles"]))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    s.close()
+    a = np.asarray(its, dtype=np.float64)
+    return {"workload": "lognormal_hhe 128^3 H+He, 16 sources, 20 steps of 5e12 s from the "
+                        "initial state, plain FP64 (FP64 multigrid)",
+            "value": w.N * w.nsteps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / w.nsteps,
+            "newton_its_per_step": float(a[:, 0].mean()),
+            "krylov_its_per_step": float(a[:, 1].mean()),
+            "vcycles_per_step": float(a[:, 2].mean()),
+            "newton_its": a[:, 0].astype(int).tolist(), "krylov_its": a[:, 1].astype(int).tolist()}
 
 
 def train_guess(rhi, torch, rank, train_steps, epochs):
@@ -423,6 +538,8 @@ def main():
                     help="steps of the 128^3 training run for the learned guess")
     ap.add_argument("--train-epochs", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-config2", action="store_true",
+                    help="skip the 128^3 plain FP64 configuration (20 steps)")
     ap.add_argument("--max-newton", type=int, default=200)
     ap.add_argument("--limiter-jacobian", type=int, default=2,
                     help="0: D lagged (CG); 1: dD/dE kept; 2: exact Newton matrix (BiCGStab)")
@@ -453,6 +570,7 @@ def main():
     nsrc = workload_sources(n)
     w = inputs.config_lognormal(n, nsrc=nsrc, seed=rank)
     hbm_peak, peak_src = load_peaks()
+    AB = alg_bytes(args.limiter_jacobian != 0)
 
     # forms: plain FP64 (FP64 multigrid), mixed (FP32 multigrid), learned + mixed (headline)
     FORMS = {"plain_fp64": (rhi.RHI_PRECOND_MG_FP64, rhi.RHI_GUESS_PREVIOUS),
@@ -471,13 +589,13 @@ def main():
         torch.cuda.synchronize()
         clk = ClockSampler(local)
         clk.start()
-        s, ms, agg, kt_timed, kt_all = run_form(
-            rhi, w, torch, args.steps, args.warmup, pc, TIMED_KERNELS,
+        s, ms, agg, kt_timed, kt_all, tname = run_form(
+            rhi, w, torch, args.steps, args.warmup, pc, AB,
             limiter_jacobian=args.limiter_jacobian, max_newton=args.max_newton, guess=guess,
             weights=weights if guess == rhi.RHI_GUESS_LEARNED else None)
         clocks = clk.stop()
         forms[name] = dict(ms=max_over_ranks(ms, dist, "cuda"), agg=agg, kt=kt_all,
-                           kt_timed=kt_timed, clocks=clocks)
+                           kt_timed=kt_timed, clocks=clocks, tname=tname)
         s.close()
         del s
         torch.cuda.empty_cache()
@@ -486,30 +604,33 @@ def main():
     ms_step = head["ms"] / args.steps
     value = replica_throughput(world, w.N, args.steps, head["ms"])
 
-    # dominant kernel (largest share of the breakdown step) and its roofline from the
-    # per-launch device times inside the timed region
+    # the dominant kernel (largest share of the breakdown step, among the kernels with a byte
+    # or flop model) and its roofline from the per-launch device times inside the timed region
     kt = head["kt"]
     tot = sum(v[0] for v in kt.values())
-    timed = {k: v for k, v in kt.items() if k in TIMED_KERNELS} or kt
-    tname = max(timed.items(), key=lambda kv: kv[1][0])[0]
-    roof = {"kernel": tname, "share": kt[tname][0] / tot if tot else None}
+    tname = head["tname"]
+    roof = {"kernel": tname, "share": kt[tname][0] / tot if tot else None,
+            "launches_breakdown_step": kt[tname][1]}
     if tname in head["kt_timed"]:
         tms, tcnt = head["kt_timed"][tname]
         avg_s = tms / tcnt * 1e-3
         roof["avg_launch_ms"] = avg_s * 1e3
         roof["launches_timed"] = tcnt
+        roof["units_per_launch"] = w.N
         if tname in ALU_FLOPS:
             ach = ALU_FLOPS[tname] * w.N / avg_s / 1e12
             roof.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                        frac=ach / FP64_PEAK_TFLOPS, traffic=TRAFFIC_PER_CELL[tname] * w.N if tname in TRAFFIC_PER_CELL else None,
+                        frac=ach / FP64_PEAK_TFLOPS,
+                        traffic=TRAFFIC_PER_CELL[tname] * w.N if tname in TRAFFIC_PER_CELL else None,
                         flops_per_cell=ALU_FLOPS[tname],
                         peak_source="derived: 152 SMs x 2070 MHz x 2 DFMA/clk/SM x 2 flop")
-        elif tname in ALG_BYTES:
-            ach = ALG_BYTES[tname] * w.N / avg_s / 1e9
+        elif tname in AB:
+            ach = AB[tname] * w.N / avg_s / 1e9
             roof.update(bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s",
-                        frac=ach / hbm_peak,
+                        frac=ach / hbm_peak, bytes_per_cell=AB[tname],
                         traffic=TRAFFIC_PER_CELL[tname] * w.N if tname in TRAFFIC_PER_CELL else None,
-                        peak_source=peak_src)
+                        peak_source=peak_src + " copy bandwidth (MEASURED_PEAKS hbm_gbs)"
+                        if peak_src == "measured" else peak_src)
     # HBM fraction of the Krylov / multigrid stencil and vector kernels (full-grid launches):
     # algorithmic bytes over the mean launch time of the profiled step, against the measured
     # copy bandwidth
@@ -518,7 +639,7 @@ def main():
         for k in LINEAR_KERNELS:
             if k in kt_f and kt_f[k][1] > 0 and kt_f[k][0] > 0:
                 ms_k, c_k = kt_f[k]
-                out[k] = ALG_BYTES[k] * w.N / (ms_k / c_k * 1e-3) / 1e9 / hbm_peak
+                out[k] = AB[k] * w.N / (ms_k / c_k * 1e-3) / 1e9 / hbm_peak
         return out
 
     lin = hbm_fracs(kt)
@@ -530,6 +651,9 @@ def main():
                    if isinstance(v, (int, float))},
                 "kernel_ms_breakdown_step": {k: v[0] for k, v in
                                              sorted(f["kt"].items(), key=lambda kv: -kv[1][0])},
+                "kernel_launches_breakdown_step": {k: v[1] for k, v in
+                                                   sorted(f["kt"].items(), key=lambda kv: -kv[1][0])},
+                "roofline_kernel": f["tname"],
                 "hbm_frac": hbm_fracs(f["kt"])}
 
     line = {
@@ -554,6 +678,9 @@ def main():
         line["speedup_vs_plain_fp64"] = forms["plain_fp64"]["ms"] / head["ms"]
     if train_info:
         line["learned_guess_training"] = train_info
+    if not args.no_config2:
+        line["config_128_plain_fp64"] = config_128_plain(rhi, torch, args.limiter_jacobian,
+                                                         args.max_newton)
     if rank == 0:
         if not args.no_e2e:
             pc, guess = FORMS[order[-1]]
@@ -563,7 +690,16 @@ def main():
             line["e2e"] = {"value": world * e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                            "d2h_bytes_per_step": d2h, "wall_ms_per_step": split}
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline_sample()
+            line["cpu_baseline"], (wsub, refs) = cpu_baseline_sample()
+            line["error_vs_oracle"] = {
+                "sample": f"{len(refs)} steps of the {wsub.nx}^3 sub-box of the cpu_baseline "
+                          "sample at the timed run's settings, against the oracle converged to "
+                          "1e-14; per field the worst over the steps of max |gpu - oracle| / "
+                          "(|oracle| + 1e-12 max|oracle|), species as fractions of their element "
+                          "(per_element), and of max |gpu - oracle| / u in the scaled unknowns "
+                          "the Newton tolerance applies to (scaled)",
+                **error_vs_oracle(rhi, {k: FORMS[k] for k in order}, wsub, refs,
+                                  args.limiter_jacobian, weights)}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -106,6 +106,15 @@ typedef struct {
     double mg_omega;        /* Jacobi weight                                                 */
     int vcycle_graph;       /* 1: the FP32 V-cycle is captured once as a CUDA graph and
                                replayed (on a library-owned stream ordered by events)       */
+    int krylov_graph;       /* 1: each BiCGStab solve runs as one CUDA graph launch, its loop a
+                               while node whose iterations decide on the device whether to
+                               continue (no host round trip per iteration); 0: the same
+                               kernels launched from the host, one read per iteration       */
+    int mg_matrix;          /* the operator the multigrid hierarchy is built from: 1 (default)
+                               the Newton matrix the Krylov method solves (with dD/dE kept a
+                               non-symmetric 7-point matrix, whose coarse levels then carry
+                               both couplings of each face); 0 the lagged-D matrix
+                               (symmetric), as a preconditioner of the Newton matrix        */
     int dt_norm;            /* adaptive time steps (Sec. 3.2.3): 0 off; p >= 1 the p-norm and
                                -1 the max norm of eq. time_error_estimator                  */
     double dt_tau_tol;      /* tau_tol of eq. time_step_selection                            */
@@ -133,6 +142,8 @@ typedef struct {
     int guess_restarts;     /* 1 when Newton abandoned the learned start for U^n (mlp_restart) */
     int krylov_fallbacks;   /* Newton iterations whose BiCGStab broke down and that took the
                                lagged-D direction (CG) instead                              */
+    int host_syncs;         /* blocking device-to-host reads the step made (residual norms,
+                               Krylov results, the final wait)                               */
     double res_initial;     /* ||f(U_0)|| (eq. rmsnorm, scaled)                              */
     double res_final;       /* ||f(U^{n+1})||                                                */
     double res_guess_prev;  /* ||f(U^n)|| when a learned guess was tried, else 0             */
@@ -147,7 +158,9 @@ typedef struct rhi_ctx* rhi_handle;
 /* Defaults: theta 0.51 (Sec. 3.2), grey m = 1, limiter on, D lagged in the Newton matrix
    (limiter_jacobian 0), tau 0.99, lam_min 1/16, growth_max 1e3, watchdog 3, max_newton 50,
    max_pcg 200, previous-step guess, FP64 multigrid with 6 levels, 2 + 2 sweeps, 16 coarse
-   sweeps, omega 0.9, V-cycle graph on, learned-guess gates mlp_gate 1e-3, mlp_ood 6,
+   sweeps, omega 0.9, V-cycle graph on, BiCGStab graph on, multigrid of the Newton matrix
+   (mg_matrix 1),
+   learned-guess gates mlp_gate 1e-3, mlp_ood 6,
    mlp_restart 12, mlp_retry 4, fixed steps (dt_norm 0) with tau_tol 0.01, scalings 1,
    kappa_floor 1e-40, mu 0.6, and the grey constants of 13.6 eV monochromatic radiation with a
    6.3e-18 cm^2 HI cross section.  n_species must be 0 (LTE model), 1 or 3.  Host computation

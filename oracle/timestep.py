@@ -65,3 +65,40 @@ def ifront_radius(x_HII, dx, octants=8):
 def ifront_analytic(t, r_S, t_rec):
     """Eq. Ifront_solution: r_I = r_S (1 - exp(-t / t_rec))^(1/3)."""
     return r_S * (1.0 - np.exp(-np.asarray(t) / t_rec)) ** (1.0 / 3.0)
+
+
+# --------------------------------------------------------------------------------------------
+# the cosmological I-front (Sec. 4.6, "Cosmological Radiative Ionization"): a source of Ndot
+# photons/s in uniform gas whose proper density falls as a^-3 in a matter-only universe of
+# deceleration parameter q0.  Times are measured by the scale factor normalised to its initial
+# value, a~ = a / a_i = (1 + z_i) / (1 + z); radii are comoving in units of the initial proper
+# Stromgren radius r_S,i (eq. SG-stromgren_radius at z_i).
+
+def sg_g(a, q0, z_i):
+    """[1 - 2 q0 + 2 q0 (1 + z_i) / a~]^(-1/2): H0 (1 + z_i) dt = g da~ (Lambda = 0)."""
+    return (1.0 - 2.0 * q0 + 2.0 * q0 * (1.0 + z_i) / np.asarray(a, dtype=np.float64)) ** -0.5
+
+
+def sg_F(a, q0, z_i):
+    """Eq. SG-F."""
+    u = 2.0 * q0 * (1.0 + z_i) / np.asarray(a, dtype=np.float64)
+    return (2.0 - 4.0 * q0 - u) * np.sqrt(1.0 - 2.0 * q0 + u)
+
+
+def sg_tau(a, lam, q0, z_i):
+    """Eq. SG-tau: the recombination depth lambda int_1^a~ a'^-3 g(a') da' in closed form."""
+    return lam / (6.0 * q0 ** 2 * (1.0 + z_i) ** 2) * (sg_F(a, q0, z_i) - sg_F(1.0, q0, z_i))
+
+
+def sg_ifront(a, lam, q0, z_i):
+    """Eq. SG-solution: r_I / r_S,i at a~ >= 1, the integral of e^tau g by adaptive quadrature
+    (with e^-tau(a~) taken inside it, so that a large lam does not overflow).
+    lam = alpha_B n_H,i / (H0 (1 + z_i))."""
+    from scipy import integrate
+    out = []
+    for ai in np.atleast_1d(np.asarray(a, dtype=np.float64)):
+        ta = sg_tau(ai, lam, q0, z_i)
+        val, _ = integrate.quad(lambda x: np.exp(sg_tau(x, lam, q0, z_i) - ta) * sg_g(x, q0, z_i),
+                                1.0, ai, epsabs=0.0, epsrel=1e-12, limit=400)
+        out.append((lam * val) ** (1.0 / 3.0))
+    return np.asarray(out)

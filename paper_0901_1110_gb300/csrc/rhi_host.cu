@@ -76,8 +76,9 @@ struct Level {
     long long N = 0;
     T* diag = nullptr;
     T* wid = nullptr;           // omega / diag (smoother)
-    T* loc = nullptr;           // diag - sum of the six faces (FP64 restriction; FP32: none)
+    T* loc = nullptr;           // diag - the row's six couplings (FP64 restriction; FP32: none)
     T* W[3] = {nullptr, nullptr, nullptr};
+    T* Wp[3] = {nullptr, nullptr, nullptr};     // non-symmetric levels only
     T* b = nullptr;
     T* x = nullptr;
     T* xt = nullptr;
@@ -128,9 +129,12 @@ struct rhi_ctx {
     // multigrid
     std::vector<Level<double>> mg64;
     std::vector<Level<float>> mg32;
-    // operator the preconditioner was set up for, and the Newton matrix when dD/dE is kept
+    // the lagged-D Schur matrix, the Newton matrix when dD/dE is kept, and the finest operator
+    // the preconditioner was last set up from (one of the two; pc_nonsym: the Newton matrix)
     Op<double> op0{};
     OpNS opns{};
+    Op<double> pc0{};
+    bool pc_nonsym = false;
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
@@ -140,10 +144,27 @@ struct rhi_ctx {
         cudaStream_t st = nullptr;
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
         double scale = 0.0;
+        bool nonsym = false;
         std::vector<float*> post;       // level buffers (x, xt) after the captured cycle
         int kernels = 0;
         bool failed = false;
     } vg;
+
+    // the BiCGStab solve as one CUDA graph (a while node whose body is one iteration),
+    // cached per set of buffers and operator scale
+    struct KGraph {
+        const void* key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        double scale = 0.0;
+        bool nonsym = false;
+        cudaGraphExec_t exec = nullptr;
+        int k_init = 0, k_body = 0;
+    };
+    std::vector<KGraph> kg;
+    cudaStream_t kst = nullptr;           // capture stream
+    bool kg_failed = false;
+    double* h_ctl = nullptr;              // pinned: S_THR, S_MAXIT of the next solve
+    int host_syncs = 0;                   // blocking device-to-host reads of the last step
+    int kg_body_kernels = 0;              // kernels per iteration of the last graph solve
 
     // learned guess: FP32 master weights, Adam moments, gradient, BF16 inference copy;
     // scratch of the training / inspection entry points grows on demand
@@ -234,6 +255,7 @@ struct Scope {
 int read_scalar(rhi_ctx* h, int slot, double* out) {
     CK(cudaMemcpyAsync(h->h_scal, h->scal, sizeof(double) * S_NSCAL, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
+    h->host_syncs += 1;
     *out = h->h_scal[slot];
     return RHI_OK;
 }
@@ -266,6 +288,8 @@ int mg_build_levels(rhi_ctx* h) {
         nx = cx; ny = cy; nz = cz;
     }
     const int nl = (int)dims.size() / 3;
+    // the hierarchy of the non-symmetric Newton matrix carries a second face array per axis
+    const bool nonsym = h->prm.mg_matrix == 1 && h->prm.limiter_jacobian != 0;
     if (h->prm.precond == RHI_PRECOND_MG_FP64) {
         h->mg64.resize(nl);
         for (int l = 0; l < nl; ++l) {
@@ -276,6 +300,8 @@ int mg_build_levels(rhi_ctx* h) {
             if (l > 0) {
                 if ((rc = dalloc(h, &v.diag, v.N))) return rc;
                 for (int a = 0; a < 3; ++a) if ((rc = dalloc(h, &v.W[a], v.N))) return rc;
+                if (nonsym)
+                    for (int a = 0; a < 3; ++a) if ((rc = dalloc(h, &v.Wp[a], v.N))) return rc;
                 if ((rc = dalloc(h, &v.b, v.N))) return rc;
                 if ((rc = dalloc(h, &v.x, v.N))) return rc;
             }
@@ -293,6 +319,8 @@ int mg_build_levels(rhi_ctx* h) {
             if ((rc = dalloc(h, &v.diag, v.N))) return rc;
             if ((rc = dalloc(h, &v.wid, v.N))) return rc;
             for (int a = 0; a < 3; ++a) if ((rc = dalloc(h, &v.W[a], v.N))) return rc;
+            if (nonsym)
+                for (int a = 0; a < 3; ++a) if ((rc = dalloc(h, &v.Wp[a], v.N))) return rc;
             if ((rc = dalloc(h, &v.b, v.N))) return rc;
             if ((rc = dalloc(h, &v.x, v.N))) return rc;
             if ((rc = dalloc(h, &v.xt, v.N))) return rc;
@@ -307,7 +335,11 @@ Op<T> level_op(const rhi_ctx* h, const Level<T>& v) {
     A.nx = v.nx; A.ny = v.ny; A.nz = v.nz; A.N = v.N;
     A.fd_nx = make_fastdiv((unsigned)v.nx);
     A.fd_nxy = make_fastdiv((unsigned)v.nx * (unsigned)v.ny);
-    for (int a = 0; a < 3; ++a) { A.per[a] = h->per[a]; A.W[a] = v.W[a]; }
+    for (int a = 0; a < 3; ++a) {
+        A.per[a] = h->per[a];
+        A.W[a] = v.W[a];
+        A.Wp[a] = h->pc_nonsym && v.Wp[a] ? v.Wp[a] : v.W[a];
+    }
     A.diag = v.diag;
     A.wid = v.wid;
     A.loc = v.loc;
@@ -315,34 +347,53 @@ Op<T> level_op(const rhi_ctx* h, const Level<T>& v) {
     return A;
 }
 
-// coarse operators for the current finest operator h->op0
-int precond_setup(rhi_ctx* h) {
+// the Newton matrix that keeps dD/dE (h->opns) as a multigrid operator: W = Q, Wp = P
+Op<double> newton_op(const rhi_ctx* h) {
+    const OpNS& B = h->opns;
+    Op<double> A{};
+    A.nx = B.nx; A.ny = B.ny; A.nz = B.nz; A.N = B.N;
+    A.fd_nx = B.fd_nx; A.fd_nxy = B.fd_nxy;
+    for (int a = 0; a < 3; ++a) { A.per[a] = B.per[a]; A.W[a] = B.Q[a]; A.Wp[a] = B.P[a]; }
+    A.diag = B.diag;
+    A.scale = B.scale;
+    return A;
+}
+
+// coarse operators for the finest operator A0 (the lagged-D matrix h->op0, or the Newton matrix
+// when nonsym); A0 becomes the preconditioner's finest operator h->pc0
+int precond_setup(rhi_ctx* h, const Op<double>& A0, bool nonsym) {
     LinLaunch L(h->st, &h->prof);
     const double om = h->prm.mg_omega;
+    h->pc0 = A0;
+    h->pc_nonsym = nonsym;
     if (h->prm.precond == RHI_PRECOND_MG_FP64) {
         auto& lv = h->mg64;
-        h->op0.wid = lv[0].wid;
-        h->op0.loc = lv[0].loc;
-        CK((L.level_prep<double, double>(h->op0, om, lv[0].wid, lv[0].loc)));
+        if (nonsym && lv.size() > 1 && !lv[1].Wp[0])
+            return fail(h, RHI_ERR_ARG, "multigrid of the Newton matrix needs params.mg_matrix = 1");
+        h->pc0.wid = lv[0].wid;
+        h->pc0.loc = lv[0].loc;
+        CK((L.level_prep<double, double>(h->pc0, om, lv[0].wid, lv[0].loc)));
         for (size_t l = 0; l + 1 < lv.size(); ++l) {
-            Op<double> A = (l == 0) ? h->op0 : level_op(h, lv[l]);
+            Op<double> A = (l == 0) ? h->pc0 : level_op(h, lv[l]);
             auto& c = lv[l + 1];
-            CK((L.coarsen<double, double>(A, c.nx, c.ny, c.nz, c.diag, c.W[0], c.W[1], c.W[2])));
+            CK((L.coarsen<double, double>(A, c.nx, c.ny, c.nz, c.diag, c.W, nonsym ? c.Wp : nullptr)));
             CK(L.diag_faces<double>(level_op(h, c), c.diag));
             CK((L.level_prep<double, double>(level_op(h, c), om, c.wid, c.loc)));
         }
     } else if (h->prm.precond == RHI_PRECOND_MG_FP32) {
         auto& lv = h->mg32;
-        CK(L.cast_op(h->op0, lv[0].diag, lv[0].W[0], lv[0].W[1], lv[0].W[2]));
+        if (nonsym && !lv[0].Wp[0])
+            return fail(h, RHI_ERR_ARG, "multigrid of the Newton matrix needs params.mg_matrix = 1");
+        CK(L.cast_op(h->pc0, lv[0].diag, lv[0].W, nonsym ? lv[0].Wp : nullptr));
         // the finest level's omega / diag from the FP64 operator (the FP32 restriction takes
         // each child's full row and needs no local part)
-        CK((L.level_prep<double, float>(h->op0, om, lv[0].wid, nullptr)));
+        CK((L.level_prep<double, float>(h->pc0, om, lv[0].wid, nullptr)));
         for (size_t l = 0; l + 1 < lv.size(); ++l) {
             auto& c = lv[l + 1];
             if (l == 0)
-                CK((L.coarsen<double, float>(h->op0, c.nx, c.ny, c.nz, c.diag, c.W[0], c.W[1], c.W[2])));
+                CK((L.coarsen<double, float>(h->pc0, c.nx, c.ny, c.nz, c.diag, c.W, nonsym ? c.Wp : nullptr)));
             else
-                CK((L.coarsen<float, float>(level_op(h, lv[l]), c.nx, c.ny, c.nz, c.diag, c.W[0], c.W[1], c.W[2])));
+                CK((L.coarsen<float, float>(level_op(h, lv[l]), c.nx, c.ny, c.nz, c.diag, c.W, nonsym ? c.Wp : nullptr)));
             CK(L.diag_faces<float>(level_op(h, c), c.diag));
             CK((L.level_prep<float, float>(level_op(h, c), om, c.wid, nullptr)));
         }
@@ -350,13 +401,22 @@ int precond_setup(rhi_ctx* h) {
     return RHI_OK;
 }
 
+// the preconditioner of the system the Krylov method solves: the Newton matrix's own
+// hierarchy when params.mg_matrix = 1 and the matrix keeps dD/dE, else the lagged-D matrix's
+int precond_setup_newton(rhi_ctx* h) {
+    const bool nonsym = h->prm.mg_matrix == 1 && h->prm.limiter_jacobian != 0 &&
+                        h->prm.precond != RHI_PRECOND_JACOBI;
+    return precond_setup(h, nonsym ? newton_op(h) : h->op0, nonsym);
+}
+
 // one V-cycle on levels l.. with right-hand side lv[l].b; result in lv[l].x
 template <typename T>
 int vcycle(rhi_ctx* h, std::vector<Level<T>>& lv, size_t l, const Op<T>& A0,
-           cudaStream_t st = nullptr, LaunchHook* hook = nullptr) {
+           cudaStream_t st = nullptr, LaunchHook* hook = nullptr, const double* skip = nullptr) {
     if (!hook) { st = h->st; hook = &h->prof; }
     LinLaunch L(st, hook);
     L.fine_N = h->N;
+    L.skip = skip;
     Level<T>& v = lv[l];
     const Op<T> A = (l == 0) ? A0 : level_op(h, v);
     const T om = (T)h->prm.mg_omega;
@@ -381,7 +441,7 @@ int vcycle(rhi_ctx* h, std::vector<Level<T>>& lv, size_t l, const Op<T>& A0,
     }
     Level<T>& c = lv[l + 1];
     CK(L.restrict_res<T>(A, v.b, v.x, c.nx, c.ny, c.nz, c.b));
-    int rc = vcycle<T>(h, lv, l + 1, A0, st, hook);
+    int rc = vcycle<T>(h, lv, l + 1, A0, st, hook, skip);
     if (rc) return rc;
     // (a sweep that reads the coarse correction on the fly measured 3.6x slower than the
     // separate prolongation and sweep at 256^3, so the two stay separate)
@@ -421,7 +481,8 @@ bool vcycle_graph_usable(const rhi_ctx* h) {
 int vcycle_graph(rhi_ctx* h, const Op<float>& A0) {
     auto& lv = h->mg32;
     auto& g = h->vg;
-    bool valid = g.exec && g.scale == (double)A0.scale && g.post.size() == 2 * lv.size();
+    bool valid = g.exec && g.scale == (double)A0.scale && g.nonsym == h->pc_nonsym &&
+                 g.post.size() == 2 * lv.size();
     for (size_t l = 0; valid && l < lv.size(); ++l)
         valid = g.post[2 * l] == lv[l].x && g.post[2 * l + 1] == lv[l].xt;
     if (!valid) {
@@ -450,6 +511,7 @@ int vcycle_graph(rhi_ctx* h, const Op<float>& A0) {
         }
         g.kernels = cnt.n;
         g.scale = (double)A0.scale;
+        g.nonsym = h->pc_nonsym;
         g.post.clear();
         for (auto& v : lv) { g.post.push_back(v.x); g.post.push_back(v.xt); }
     }
@@ -468,13 +530,13 @@ int precond_apply(rhi_ctx* h, const double* r, double** zout, int& nparts) {
     LinLaunch L(h->st, &h->prof);
     const long long N = h->N;
     if (h->prm.precond == RHI_PRECOND_JACOBI) {
-        CK(L.jacobi_dot(N, r, h->op0.diag, h->z, h->partials, nparts));
+        CK(L.jacobi_dot(N, r, h->pc0.diag, h->z, h->partials, nparts));
         *zout = h->z;
     } else if (h->prm.precond == RHI_PRECOND_MG_FP64) {
         auto& lv = h->mg64;
         lv[0].b = const_cast<double*>(r);
         lv[0].x = h->z;
-        int rc = vcycle<double>(h, lv, 0, h->op0);
+        int rc = vcycle<double>(h, lv, 0, h->pc0);
         if (rc) return rc;
         // the result may sit in either level-0 buffer
         double* R = lv[0].x;
@@ -532,55 +594,213 @@ int pcg(rhi_ctx* h, const double* rhs, double tol, int* its_out) {
     return RHI_OK;
 }
 
-// Right-preconditioned BiCGStab on the non-symmetric Schur matrix h->opns (dD/dE kept), with
-// the symmetric lagged-D V-cycle as preconditioner; stops at ||r||_RMS <= tol; solution in h->x.
-int bicgstab(rhi_ctx* h, const double* rhs, double tol, int* its_out) {
-    LinLaunch L(h->st, &h->prof);
+// M^-1 r into dest with the launcher's stream, hook and skip flag (the second half of a
+// BiCGStab iteration); the V-cycle's kernels are launched one by one (also while a graph is
+// being captured)
+int precond_into(rhi_ctx* h, LinLaunch& L, const double* r, double* dest) {
     const long long N = h->N;
-    const double norm = 1.0 / ((double)N * h->nv);
-    int np = 0;
-    CK(cudaMemsetAsync(h->scal + S_BREAK, 0, sizeof(double), h->st));     // clear an old breakdown
-    CK(L.bicg_init(N, rhs, h->r, h->rh, h->x, h->partials, np));
-    CK(L.reduce(h->partials, np, h->scal, RED_SUM, S_RR));
-    double rr;
-    int rc = read_scalar(h, S_RR, &rr);
-    if (rc) return rc;
-    h->h_scal[S_RHO] = rr;     // rho_0 = rh.r = r.r
-    CK(cudaMemcpyAsync(h->scal + S_RHO, &h->h_scal[S_RHO], sizeof(double), cudaMemcpyHostToDevice, h->st));
-    int its = 0;
-    if (std::sqrt(rr * norm) > tol) {
-        for (its = 1; its <= h->prm.max_pcg; ++its) {
-            CK(L.bicg_p(N, h->scal, h->r, h->v, h->p, its == 1));
-            double* z = nullptr;
-            if ((rc = precond_apply(h, h->p, &z, np))) return rc;
-            std::swap(h->ph, h->z);                              // ph = M^-1 p
-            CK(L.matvec_ns(h->opns, h->ph, h->v, h->rh, 0, h->partials, np));
-            CK(L.reduce(h->partials, np, h->scal, RED_BICG_ALPHA, 0));
-            CK(L.bicg_s(N, h->scal, h->r, h->v, h->s, h->partials, np));
-            CK(L.reduce(h->partials, np, h->scal, RED_SUM, S_SS));
-            double ss;
-            if ((rc = read_scalar(h, S_SS, &ss))) return rc;
-            if (h->h_scal[S_BREAK] != 0.0 || !std::isfinite(ss))
-                return fail(h, RHI_ERR_NONPHYSICAL, "BiCGStab breakdown");
-            if (std::sqrt(ss * norm) <= tol) {                  // x += alpha ph
-                CK(L.axpy(N, h->scal, S_ALPHA, h->ph, h->x));
-                break;
-            }
-            if ((rc = precond_apply(h, h->s, &z, np))) return rc;
-            std::swap(h->sh, h->z);                              // sh = M^-1 s
-            CK(L.matvec_ns(h->opns, h->sh, h->t, h->s, 1, h->partials, np));
-            CK(L.reduce(h->partials, np, h->scal, RED_BICG_OMEGA, 0));
-            CK(L.bicg_xr(N, h->scal, h->x, h->ph, h->sh, h->s, h->t, h->r, h->rh, h->partials, np));
-            CK(L.reduce(h->partials, np, h->scal, RED_BICG_RHO, 0));
-            if ((rc = read_scalar(h, S_RR, &rr))) return rc;
-            if (h->h_scal[S_BREAK] != 0.0 || !std::isfinite(rr))
-                return fail(h, RHI_ERR_NONPHYSICAL, "BiCGStab breakdown");
-            if (std::sqrt(rr * norm) <= tol) break;
-        }
-        if (its > h->prm.max_pcg) its = h->prm.max_pcg;
+    if (h->prm.precond == RHI_PRECOND_JACOBI) {
+        int np = 0;
+        CK(L.jacobi_dot(N, r, h->pc0.diag, dest, h->partials, np));
+    } else if (h->prm.precond == RHI_PRECOND_MG_FP64) {
+        auto& lv = h->mg64;
+        double* xt0 = lv[0].xt;
+        lv[0].b = const_cast<double*>(r);
+        lv[0].x = dest;
+        int rc = vcycle<double>(h, lv, 0, h->pc0, L.st, L.hook, L.skip);
+        if (rc) return rc;
+        if (lv[0].x != dest) CK(L.copy(N, lv[0].x, dest));     // odd number of swaps
+        lv[0].x = nullptr;
+        lv[0].xt = xt0;
+    } else {
+        auto& lv = h->mg32;
+        CK(L.to_f32(N, r, lv[0].b));
+        int rc = vcycle<float>(h, lv, 0, level_op(h, lv[0]), L.st, L.hook, L.skip);
+        if (rc) return rc;
+        CK(L.from_f32(N, lv[0].x, dest));
     }
-    *its_out = its;
     return RHI_OK;
+}
+
+// r = b, rh = b, x = 0 and the loop's start (S_RR = S_RHO = r.r, counters cleared)
+int bicg_start(rhi_ctx* h, LinLaunch& L, const double* rhs, unsigned long long cond) {
+    int np = 0;
+    L.skip = nullptr;
+    CK(L.bicg_init(h->N, rhs, h->r, h->rh, h->x, h->partials, np));
+    CK(L.reduce_loop(h->partials, np, h->scal, RED_BICG_START, cond));
+    return RHI_OK;
+}
+
+// One iteration of right-preconditioned BiCGStab on the Newton matrix h->opns with every
+// decision on the device: p, M^-1 p, v = A M^-1 p, alpha, s and its convergence test; then,
+// skipped when s has converged or a breakdown occurred, M^-1 s, t = A M^-1 s and omega; the x /
+// r update; the next rho, beta and the continue flag (cond: the graph's while handle, or 0).
+int bicg_iteration(rhi_ctx* h, LinLaunch& L, unsigned long long cond) {
+    const long long N = h->N;
+    int np = 0, rc;
+    L.skip = nullptr;
+    CK(L.bicg_p(N, h->scal, h->r, h->v, h->p, -1));
+    if ((rc = precond_into(h, L, h->p, h->ph))) return rc;
+    CK(L.matvec_ns(h->opns, h->ph, h->v, h->rh, 0, h->partials, np));
+    CK(L.reduce(h->partials, np, h->scal, RED_BICG_ALPHA, 0));
+    CK(L.bicg_s(N, h->scal, h->r, h->v, h->s, h->partials, np));
+    CK(L.reduce_loop(h->partials, np, h->scal, RED_BICG_SS, 0));
+    L.skip = h->scal + S_DONE;
+    if ((rc = precond_into(h, L, h->s, h->sh))) return rc;
+    CK(L.matvec_ns(h->opns, h->sh, h->t, h->s, 1, h->partials, np));
+    CK(L.reduce(h->partials, np, h->scal, RED_BICG_OMEGA, 0));
+    L.skip = nullptr;
+    CK(L.bicg_xr_loop(N, h->scal, h->x, h->ph, h->sh, h->s, h->t, h->r, h->rh, h->partials, np));
+    CK(L.reduce_loop(h->partials, np, h->scal, RED_BICG_NEXT, cond));
+    return RHI_OK;
+}
+
+// the solve's graph is used unless per-launch timing of one of its kernels is requested
+bool krylov_graph_usable(const rhi_ctx* h) {
+    if (!h->prm.krylov_graph || h->kg_failed) return false;
+    if (!h->prof.on) return true;
+    if (h->prof.only.empty()) return false;
+    for (const auto& nm : h->prof.only)
+        if (nm.compare(0, 3, "mg_") == 0 || nm.compare(0, 5, "bicg_") == 0 || nm == "reduce" ||
+            nm == "copy" || nm == "precond_jacobi")
+            return false;
+    return true;
+}
+
+// Captures the whole solve: the start kernels, then a while node (default 1, reset at every
+// launch) whose body is one iteration; the last kernel of the start and of each iteration
+// writes the node's condition.  The body graph is filled by a second capture.
+int krylov_graph_build(rhi_ctx* h, const double* rhs, rhi_ctx::KGraph& g) {
+    if (!h->kst) CK(cudaStreamCreateWithFlags(&h->kst, cudaStreamNonBlocking));
+    Counter cnt;
+    LinLaunch L(h->kst, &cnt);
+    L.fine_N = h->N;
+    cudaGraph_t graph = nullptr, body = nullptr;
+    cudaGraphConditionalHandle hc = 0;
+    cudaStreamCaptureStatus stt;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    auto abort_capture = [&](const char* what, cudaError_t e) {
+        cudaGraph_t tmp = nullptr;
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(h->kst, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+            cudaStreamEndCapture(h->kst, &tmp);
+        if (tmp) cudaGraphDestroy(tmp);
+        if (graph && graph != tmp) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        h->kg_failed = true;
+        return fail(h, RHI_ERR_CUDA, std::string("Krylov graph: ") + what + ": " + cudaGetErrorString(e));
+    };
+    cudaError_t e = cudaStreamBeginCapture(h->kst, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return abort_capture("begin capture", e);
+    e = cudaStreamGetCaptureInfo(h->kst, &stt, nullptr, &graph, &deps, nullptr, &nd);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hc, graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return abort_capture("conditional handle", e);
+    int rc = bicg_start(h, L, rhs, (unsigned long long)hc);
+    if (rc) { abort_capture("start kernels", cudaGetLastError()); return rc; }
+    e = cudaStreamGetCaptureInfo(h->kst, &stt, nullptr, &graph, &deps, nullptr, &nd);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wn = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&wn, graph, deps, nullptr, nd, &cp);
+    if (e == cudaSuccess)
+        e = cudaStreamUpdateCaptureDependencies(h->kst, &wn, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) return abort_capture("while node", e);
+    e = cudaStreamEndCapture(h->kst, &graph);
+    if (e != cudaSuccess || !graph) return abort_capture("end capture", e);
+    const int k_init = cnt.n;
+    body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(h->kst, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return abort_capture("begin body capture", e);
+    rc = bicg_iteration(h, L, (unsigned long long)hc);
+    if (rc) { abort_capture("body kernels", cudaGetLastError()); return rc; }
+    e = cudaStreamEndCapture(h->kst, &body);
+    if (e != cudaSuccess) return abort_capture("end body capture", e);
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    graph = nullptr;
+    if (e != cudaSuccess) { g.exec = nullptr; return abort_capture("instantiate", e); }
+    g.k_init = k_init;
+    g.k_body = cnt.n - k_init;
+    return RHI_OK;
+}
+
+// the outcome of the last BiCGStab solve from the host copy of the scalars (h->h_scal, filled
+// by the read that followed the solve): iterations, multigrid cycles, breakdown
+int bicg_outcome(rhi_ctx* h, int* its_out) {
+    const int its = (int)h->h_scal[S_ITS];
+    *its_out = its;
+    h->prof.launches += its * h->kg_body_kernels;
+    h->kg_body_kernels = 0;
+    if (h->prm.precond != RHI_PRECOND_JACOBI)
+        h->stats.vcycles += 2 * its - (h->h_scal[S_HALF] != 0.0 ? 1 : 0);
+    if (h->h_scal[S_BREAK] != 0.0 || !std::isfinite(h->h_scal[S_RR]))
+        return fail(h, RHI_ERR_NONPHYSICAL, "BiCGStab breakdown");
+    return RHI_OK;
+}
+
+// Right-preconditioned BiCGStab on the non-symmetric Schur matrix h->opns (dD/dE kept), to
+// ||r||_RMS <= tol (counted over the N (N_s + 2) unknowns of eq. rmsnorm); solution in h->x.
+// The iteration's control runs on the device: as one CUDA graph launch per solve, or, while
+// per-launch timing is on, as direct launches with one host read per iteration.  With
+// `deferred` and the graph, the call only enqueues the solve (*its_out = -1): the next host
+// read of the scalars brings its outcome back for bicg_outcome.  Otherwise the outcome is read
+// here; RHI_ERR_NONPHYSICAL on a breakdown.
+int bicgstab(rhi_ctx* h, const double* rhs, double tol, int* its_out, bool deferred = false) {
+    const long long N = h->N;
+    h->h_ctl[0] = tol * tol * (double)N * h->nv;                   // S_THR: bound on r.r
+    h->h_ctl[1] = (double)h->prm.max_pcg;                           // S_MAXIT
+    CK(cudaMemcpyAsync(h->scal + S_THR, h->h_ctl, 2 * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    int rc = RHI_OK;
+    if (krylov_graph_usable(h)) {
+        const void* key[6] = {rhs, h->opns.diag, h->opns.P[0], h->pc0.diag, h->pc0.W[0],
+                              (const void*)(long long)h->prm.precond};
+        rhi_ctx::KGraph* g = nullptr;
+        for (auto& c : h->kg)
+            if (std::equal(key, key + 6, c.key) && c.scale == h->opns.scale && c.nonsym == h->pc_nonsym)
+                g = &c;
+        if (!g) {
+            if (h->kg.size() >= 8) {
+                for (auto& c : h->kg) if (c.exec) cudaGraphExecDestroy(c.exec);
+                h->kg.clear();
+            }
+            rhi_ctx::KGraph ng;
+            std::copy(key, key + 6, ng.key);
+            ng.scale = h->opns.scale;
+            ng.nonsym = h->pc_nonsym;
+            if ((rc = krylov_graph_build(h, rhs, ng))) return rc;
+            h->kg.push_back(ng);
+            g = &h->kg.back();
+        }
+        {
+            Scope s(h->prof, "krylov_graph");
+            CK(cudaGraphLaunch(g->exec, h->st));
+        }
+        // launches: the start kernels now, the iterations' when the count is read back
+        h->prof.launches += g->k_init - 1;              // the scope counted one
+        h->kg_body_kernels = g->k_body;
+        if (deferred) {
+            *its_out = -1;
+            return RHI_OK;
+        }
+        double dummy;
+        if ((rc = read_scalar(h, S_ITS, &dummy))) return rc;
+    } else {
+        h->kg_body_kernels = 0;                         // direct launches count themselves
+        LinLaunch L(h->st, &h->prof);
+        L.fine_N = N;
+        if ((rc = bicg_start(h, L, rhs, 0))) return rc;
+        double cont = 0.0;
+        if ((rc = read_scalar(h, S_CONT, &cont))) return rc;
+        while (cont != 0.0) {
+            if ((rc = bicg_iteration(h, L, 0))) return rc;
+            if ((rc = read_scalar(h, S_CONT, &cont))) return rc;
+        }
+    }
+    return bicg_outcome(h, its_out);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -627,7 +847,7 @@ void set_op0(rhi_ctx* h, const StepParams& P, int set, const double* W) {
     A.nx = h->grid.nx; A.ny = h->grid.ny; A.nz = h->grid.nz; A.N = h->N;
     A.fd_nx = make_fastdiv((unsigned)A.nx);
     A.fd_nxy = make_fastdiv((unsigned)A.nx * (unsigned)A.ny);
-    for (int a = 0; a < 3; ++a) { A.per[a] = h->per[a]; A.W[a] = W + a * h->N; }
+    for (int a = 0; a < 3; ++a) { A.per[a] = h->per[a]; A.W[a] = A.Wp[a] = W + a * h->N; }
     A.diag = h->diag[set];
     A.scale = P.dth;
 }
@@ -672,6 +892,8 @@ int validate_params(const rhi_params* p) {
     if (p->precond < 0 || p->precond > RHI_PRECOND_MG_FP32) return 0;
     if (p->mg_levels < 1 || p->mg_pre < 1 || p->mg_post < 0 || p->mg_coarse_sweeps < 1) return 0;
     if (p->limiter_jacobian < 0 || p->limiter_jacobian > 2) return 0;
+    if (p->mg_matrix != 0 && p->mg_matrix != 1) return 0;
+    if (p->krylov_graph != 0 && p->krylov_graph != 1) return 0;
     if (!(p->mg_omega > 0.0 && p->mg_omega <= 1.0)) return 0;
     if (p->vcycle_graph != 0 && p->vcycle_graph != 1) return 0;
     if (p->dt_norm < -1 || !(p->dt_tau_tol > 0.0)) return 0;
@@ -782,6 +1004,8 @@ int rhi_params_default(rhi_params* p, int n_species) {
     p->mg_coarse_sweeps = 16;
     p->mg_omega = 0.9;
     p->vcycle_graph = 1;
+    p->mg_matrix = 1;
+    p->krylov_graph = 1;
     p->dt_norm = 0;
     p->dt_tau_tol = 0.01;
     p->model = n_species == 0 ? RHI_MODEL_LTE : RHI_MODEL_IONIZATION;
@@ -849,6 +1073,7 @@ int rhi_create(const rhi_grid* grid, const rhi_bc* bc, const rhi_params* params,
     if (!rc) rc = mg_build_levels(h);
     if (!rc) {
         cudaError_t e = cudaMallocHost(&h->h_scal, sizeof(double) * S_NSCAL);
+        if (e == cudaSuccess) e = cudaMallocHost(&h->h_ctl, sizeof(double) * 2);
         if (e != cudaSuccess) rc = fail(h, RHI_ERR_CUDA, "cudaMallocHost");
     }
     if (!rc) {
@@ -875,6 +1100,10 @@ void rhi_destroy(rhi_handle h) {
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
     if (h->h_scal) cudaFreeHost(h->h_scal);
+    if (h->h_ctl) cudaFreeHost(h->h_ctl);
+    if (h->kst) cudaStreamSynchronize(h->kst);
+    for (auto& c : h->kg) if (c.exec) cudaGraphExecDestroy(c.exec);
+    if (h->kst) cudaStreamDestroy(h->kst);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->vg.st) cudaStreamSynchronize(h->vg.st);
@@ -1032,7 +1261,7 @@ int rhi_linearize(rhi_handle h, double dt, double a, double adot, double* f, dou
     if ((rc = schur_kappa(h, P, 0, 0))) return rc;
     set_op0(h, P, 0, h->W[0]);
     if (h->prm.limiter_jacobian) set_opns(h, P, 0, h->PQ[0]);
-    if ((rc = precond_setup(h))) return rc;
+    if ((rc = precond_setup_newton(h))) return rc;
     const long long N = h->N;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (f && !on_device) CK(cudaMemcpyAsync(f, h->U[1], (size_t)h->nv * N * sizeof(double), kind, h->st));
@@ -1142,6 +1371,7 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
     rhi_stats& S = h->stats;
     S = rhi_stats{};
     S.status = RHI_OK;
+    h->host_syncs = 0;
     const int launches0 = h->prof.launches;
     const StepParams P = make_params(h, dt, a, adot);
     const long long N = h->N;
@@ -1247,25 +1477,29 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
         const double* Wk = h->W[cur < 0 ? 0 : cur];
         if ((rc = schur_kappa(h, P, cur < 0 ? 0 : cur, set))) return rc;
         set_op0(h, P, set, Wk);
-        if ((rc = precond_setup(h))) return rc;
+        if (h->prm.limiter_jacobian) set_opns(h, P, set, h->PQ[cur < 0 ? 0 : cur]);
+        if ((rc = precond_setup_newton(h))) return rc;
         int its = 0;
+        // BiCGStab broke down (where free streaming makes the advective part of the matrix
+        // dominate): this Newton iteration takes the direction of the symmetric lagged-D
+        // matrix instead, solved by CG with that matrix's V-cycle
+        auto krylov_fallback = [&]() -> int {
+            S.krylov_fallbacks += 1;
+            S.pcg_its += its;
+            int r2;
+            if (h->pc_nonsym && (r2 = precond_setup(h, h->op0, false))) return r2;
+            return pcg(h, h->rhs[set], lin_tol * res, &its);
+        };
+        bool deferred = false;
         if (h->prm.limiter_jacobian) {
-            set_opns(h, P, set, h->PQ[cur < 0 ? 0 : cur]);
-            rc = bicgstab(h, h->rhs[set], lin_tol * res, &its);
-            if (rc == RHI_ERR_NONPHYSICAL) {
-                // BiCGStab broke down (where free streaming makes the advective part of the
-                // matrix dominate): this Newton iteration takes the direction of the
-                // symmetric lagged-D matrix instead, solved by CG
-                S.krylov_fallbacks += 1;
-                S.pcg_its += its;
-                rc = pcg(h, h->rhs[set], lin_tol * res, &its);
-            }
+            rc = bicgstab(h, h->rhs[set], lin_tol * res, &its, true);
+            deferred = rc == RHI_OK && its < 0;
+            if (rc == RHI_ERR_NONPHYSICAL) rc = krylov_fallback();
             if (rc) { S.status = rc; return rc; }
         } else if ((rc = pcg(h, h->rhs[set], lin_tol * res, &its))) {
             S.status = rc;
             return rc;
         }
-        S.pcg_its += its;
         const int t = (cur == 0) ? 1 : 0;
         const double* ec0 = cur < 0 ? nullptr : U_ec(h, cur);
         const double* n0 = cur < 0 ? h->n_s : U_n(h, cur);
@@ -1291,6 +1525,18 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
         // `watchdog` iterations without a new best ||f||, else Armijo backtracking
         double rt = 0.0;
         if ((rc = trial(1.0, &rt))) return rc;
+        if (deferred) {
+            // the full step's residual read also brought the Krylov solve's outcome back
+            rc = bicg_outcome(h, &its);
+            if (rc == RHI_ERR_NONPHYSICAL) {
+                if ((rc = krylov_fallback())) { S.status = rc; return rc; }
+                if ((rc = trial(1.0, &rt))) return rc;
+            } else if (rc) {
+                S.status = rc;
+                return rc;
+            }
+        }
+        S.pcg_its += its;
         if (rt <= (1.0 - 1e-4) * r_best) {
             r_best = rt;
             bad = 0;
@@ -1361,6 +1607,7 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     S.ms = ms;
     S.launches = h->prof.launches - launches0;
+    S.host_syncs = h->host_syncs + 1;          // and the final event wait
     h->prof.resolve();
     return RHI_OK;
 }

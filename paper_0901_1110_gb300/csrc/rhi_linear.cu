@@ -3,13 +3,18 @@
 // precision form) or by Jacobi.  Reductions are deterministic: per-block partial sums are
 // added in a fixed order by a single block.
 //
-// Operator of a level: (A x)_c = diag_c x_c - scale * sum_faces W_f x_nb(f), where W holds the
-// coefficient of each cell's lower face per axis (0 on zero-flux boundary faces).
+// Operator of a level: (A x)_c = diag_c x_c - scale * sum_ax (W[ax]_c x_lo + Wp[ax]_hi x_hi),
+// stored per lower face (0 on zero-flux boundary faces): W couples the upper cell's row to the
+// lower cell, Wp the lower cell's row to the upper cell.  Symmetric levels pass Wp = W.
 #include "rhi_linear.cuh"
 
 namespace rhi {
 
 constexpr int LIN_BLOCK = 256;
+constexpr int RED_BLOCK = 1024;
+
+// the second half of a converged BiCGStab iteration returns at once
+__device__ __forceinline__ bool skipped(const double* skip) { return skip && *skip != 0.0; }
 
 int stream_blocks(long long N) {
     const long long want = (N + LIN_BLOCK - 1) / LIN_BLOCK;
@@ -62,7 +67,7 @@ __device__ __forceinline__ T off_row(const Op<T>& A, const TX* __restrict__ x, l
         else { hi = c; has_hi = false; }
         const T wlo = A.W[ax][c];
         off += wlo * T(x[lo]);
-        if (has_hi) off += A.W[ax][hi] * T(x[hi]);
+        if (has_hi) off += A.Wp[ax][hi] * T(x[hi]);
     }
     return off;
 }
@@ -135,7 +140,9 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_cg_p(long long N, const double* _
 __global__ void __launch_bounds__(LIN_BLOCK) k_jacobi_dot(long long N, const double* __restrict__ r,
                                                           const double* __restrict__ diag,
                                                           double* __restrict__ z,
-                                                          double* __restrict__ partials) {
+                                                          double* __restrict__ partials,
+                                                          const double* skip) {
+    if (skipped(skip)) return;
     double acc = 0.0;
     for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
          c += (long long)gridDim.x * LIN_BLOCK) {
@@ -181,10 +188,10 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_cg_init(long long N, const double
 //   SUM_TO(k):   scal[k] = sum
 //   SUM_ALPHA:   scal[S_PQ] = sum; scal[S_ALPHA] = scal[S_RZ] / sum (breakdown flag if <= 0)
 //   SUM_BETA:    scal[S_BETA] = sum / scal[S_RZ]; scal[S_RZ] = sum
-constexpr int RED_BLOCK = 1024;
 __global__ void __launch_bounds__(RED_BLOCK) k_reduce(const double* __restrict__ partials, int n,
                                                       double* __restrict__ scal, int op,
-                                                      int slot) {
+                                                      int slot, const double* skip) {
+    if (skipped(skip)) return;
     // the BiCGStab updates carry a second set of partials after the first n
     const bool two = op == RED_BICG_OMEGA || op == RED_BICG_RHO;
     if (op == RED_MAX) {                        // max of non-negative partials
@@ -247,6 +254,7 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_matvec_ns(const OpNS A, const dou
                                                          double* __restrict__ y,
                                                          const double* __restrict__ w1,
                                                          double* __restrict__ partials) {
+    if (skipped(A.skip)) return;
     double d1 = 0.0, d2 = 0.0;
     const long long sz = (long long)A.nx * A.ny;
     for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < A.N;
@@ -304,6 +312,7 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_bicg_p(long long N, const double*
                                                       const double* __restrict__ v,
                                                       double* __restrict__ p, int first) {
     const double beta = scal[S_BETA], omega = scal[S_OMEGA];
+    if (first < 0) first = scal[S_ITS] == 0.0;
     for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
          c += (long long)gridDim.x * LIN_BLOCK)
         p[c] = first ? r[c] : r[c] + beta * (p[c] - omega * v[c]);
@@ -363,6 +372,127 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_axpy(long long N, const double* _
         x[c] += a * p[c];
 }
 
+// x / r update of the device-controlled loop.  Converged at the middle of the iteration
+// (S_HALF): x += alpha ph, r untouched.  Otherwise, unless a breakdown ended the iteration:
+// x += alpha ph + omega sh, r = s - omega t, partials r.r then rh.r (zeros when skipped)
+__global__ void __launch_bounds__(LIN_BLOCK) k_bicg_xr_loop(long long N,
+                                                            const double* __restrict__ scal,
+                                                            double* __restrict__ x,
+                                                            const double* __restrict__ ph,
+                                                            const double* __restrict__ sh,
+                                                            const double* __restrict__ s,
+                                                            const double* __restrict__ t,
+                                                            double* __restrict__ r,
+                                                            const double* __restrict__ rh,
+                                                            double* __restrict__ partials) {
+    const double alpha = scal[S_ALPHA], omega = scal[S_OMEGA];
+    const bool half = scal[S_HALF] != 0.0;
+    const bool none = !half && scal[S_DONE] != 0.0;
+    double rr = 0.0, rhr = 0.0;
+    if (!none) {
+        for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+             c += (long long)gridDim.x * LIN_BLOCK) {
+            if (half) {
+                x[c] += alpha * ph[c];
+            } else {
+                x[c] += alpha * ph[c] + omega * sh[c];
+                const double rv = s[c] - omega * t[c];
+                r[c] = rv;
+                rr += rv * rv;
+                rhr += rh[c] * rv;
+            }
+        }
+    }
+    const double a1 = block_sum<LIN_BLOCK>(rr);
+    if (threadIdx.x == 0) partials[blockIdx.x] = a1;
+    const double a2 = block_sum<LIN_BLOCK>(rhr);
+    if (threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = a2;
+}
+
+// z = x widened to FP64
+__global__ void __launch_bounds__(LIN_BLOCK) k_from_f32(long long N, const float* __restrict__ x,
+                                                        double* __restrict__ z,
+                                                        const double* skip) {
+    if (skipped(skip)) return;
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+         c += (long long)gridDim.x * LIN_BLOCK)
+        z[c] = (double)x[c];
+}
+
+__global__ void __launch_bounds__(LIN_BLOCK) k_copy(long long N, const double* __restrict__ a,
+                                                    double* __restrict__ b, const double* skip) {
+    if (skipped(skip)) return;
+    for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
+         c += (long long)gridDim.x * LIN_BLOCK)
+        b[c] = a[c];
+}
+
+// The reductions of the device-controlled BiCGStab loop: a fixed-order sum of the partials
+// (two sets for RED_BICG_NEXT), then the loop's scalar logic, and the continue flag written to
+// S_CONT and, inside a CUDA graph, to the while node's conditional handle.
+//   RED_BICG_START: r.r of r = b: S_RR = S_RHO = r.r, counters cleared; done when
+//                   r.r <= S_THR (or not finite: breakdown).
+//   RED_BICG_SS:    s.s: converged at the middle of the iteration when s.s <= S_THR (S_HALF,
+//                   S_DONE); a breakdown flagged by the alpha reduction also sets S_DONE.
+//   RED_BICG_NEXT:  r.r and rh.r: beta and rho for the next iteration, S_ITS += 1, and the
+//                   loop ends when converged (or S_DONE), on a breakdown, or at S_MAXIT.
+// This kernel always runs to its end: it is what ends the loop.
+__global__ void __launch_bounds__(RED_BLOCK) k_reduce_loop(const double* __restrict__ partials,
+                                                           int n, double* __restrict__ scal,
+                                                           int op, unsigned long long cond) {
+    const bool two = op == RED_BICG_NEXT;
+    double acc = 0.0, acc2 = 0.0;
+    for (int q = threadIdx.x; q < n; q += RED_BLOCK) {
+        acc += partials[q];
+        if (two) acc2 += partials[n + q];
+    }
+    const double s = block_sum<RED_BLOCK>(acc);
+    const double s2 = two ? block_sum<RED_BLOCK>(acc2) : 0.0;
+    if (threadIdx.x != 0) return;
+    int cont = 0;
+    if (op == RED_BICG_START) {
+        const bool fin = isfinite(s);
+        scal[S_RR] = s;
+        scal[S_RHO] = s;
+        scal[S_ITS] = 0.0;
+        scal[S_HALF] = 0.0;
+        scal[S_BREAK] = fin ? 0.0 : 1.0;
+        const bool done = !(s > scal[S_THR]) || !fin || !(scal[S_MAXIT] >= 1.0);
+        scal[S_DONE] = done ? 1.0 : 0.0;
+        cont = !done;
+    } else if (op == RED_BICG_SS) {
+        scal[S_SS] = s;
+        if (!isfinite(s)) {
+            scal[S_BREAK] = 1.0;
+            scal[S_DONE] = 1.0;
+        } else if (scal[S_BREAK] != 0.0) {
+            scal[S_DONE] = 1.0;
+        } else if (!(s > scal[S_THR])) {
+            scal[S_HALF] = 1.0;
+            scal[S_DONE] = 1.0;
+        }
+        return;                                    // no loop decision here
+    } else {                                       // RED_BICG_NEXT
+        const double its = scal[S_ITS] + 1.0;
+        scal[S_ITS] = its;
+        if (scal[S_DONE] != 0.0) {
+            cont = 0;
+        } else {
+            const double rho = s2;
+            scal[S_RR] = s;
+            scal[S_BETA] = (rho / scal[S_RHO]) * (scal[S_ALPHA] / scal[S_OMEGA]);
+            scal[S_RHO] = rho;
+            const bool brk = !isfinite(s) || !(rho != 0.0) || scal[S_BREAK] != 0.0;
+            if (brk) scal[S_BREAK] = 1.0;
+            const bool conv = !(s > scal[S_THR]);
+            // (written so that a cap that is not a number also ends the loop)
+            cont = !(conv || brk) && its < scal[S_MAXIT] && its < 1e6;
+        }
+    }
+    scal[S_CONT] = cont ? 1.0 : 0.0;
+    if (cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, cont ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------------------------------------
 // multigrid kernels (templated on the level precision)
 
@@ -373,6 +503,7 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_smooth(const Op<T> A, const T*
                                                          const T* __restrict__ xin,
                                                          T* __restrict__ xout, T omega,
                                                          int first) {
+    if (skipped(A.skip)) return;
     for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < A.N;
          c += (long long)gridDim.x * LIN_BLOCK) {
         const T wi = A.wid[c];
@@ -397,6 +528,7 @@ template <typename T>
 __global__ void __launch_bounds__(LIN_BLOCK) k_mg_smooth_zm(const Op<T> A, const T* __restrict__ b,
                                                             const T* __restrict__ xin,
                                                             T* __restrict__ xout, T omega) {
+    if (skipped(A.skip)) return;
     const long long nxy = (long long)A.nx * A.ny;
     const long long col = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x;
     if (col >= nxy) return;
@@ -416,29 +548,35 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_smooth_zm(const Op<T> A, const
     const T* __restrict__ W0 = A.W[0];
     const T* __restrict__ W1 = A.W[1];
     const T* __restrict__ W2 = A.W[2];
+    const T* __restrict__ P0 = A.Wp[0];
+    const T* __restrict__ P1 = A.Wp[1];
+    const T* __restrict__ P2 = A.Wp[2];
     const T* __restrict__ wd = A.wid;
     // z: plane below k0 (the far side when k0 = 0: W = 0 there unless periodic).  All loads of
     // the ZM planes are issued first (registers), then the planes are computed in order;
     // the launcher uses this kernel only when ZM divides nz.
     const long long c0 = col + (long long)k0 * nxy;
     const long long ctop = k0 + ZM < nz ? c0 + (long long)ZM * nxy : col;   // plane above
-    T xz[ZM + 2], wz[ZM + 1], w0l[ZM], w0h[ZM], w1l[ZM], w1h[ZM], x0l[ZM], x0h[ZM], x1l[ZM],
+    // wz: the lower-face coupling of each plane's row; pz: the coupling of each plane's row to
+    // the plane above (Wp of the face above; the same numbers as wz[kk + 1] when symmetric)
+    T xz[ZM + 2], wz[ZM], pz[ZM], w0l[ZM], w0h[ZM], w1l[ZM], w1h[ZM], x0l[ZM], x0h[ZM], x1l[ZM],
         x1h[ZM], dd[ZM], bb[ZM];
     xz[0] = __ldg(xin + (k0 > 0 ? c0 - nxy : col + (long long)(nz - 1) * nxy));
     xz[ZM + 1] = __ldg(xin + ctop);
-    wz[ZM] = __ldg(W2 + ctop);
 #pragma unroll
     for (int kk = 0; kk < ZM; ++kk) {
         const long long c = c0 + (long long)kk * nxy;
+        const long long cu = kk + 1 < ZM ? c + nxy : ctop;
         xz[kk + 1] = __ldg(xin + c);
         wz[kk] = __ldg(W2 + c);
+        pz[kk] = __ldg(P2 + cu);
         w0l[kk] = __ldg(W0 + c);
         x0l[kk] = __ldg(xin + c + dlo0);
-        w0h[kk] = hhi0 ? __ldg(W0 + c + dhi0) : T(0);
+        w0h[kk] = hhi0 ? __ldg(P0 + c + dhi0) : T(0);
         x0h[kk] = hhi0 ? __ldg(xin + c + dhi0) : T(0);
         w1l[kk] = __ldg(W1 + c);
         x1l[kk] = __ldg(xin + c + dlo1);
-        w1h[kk] = hhi1 ? __ldg(W1 + c + dhi1) : T(0);
+        w1h[kk] = hhi1 ? __ldg(P1 + c + dhi1) : T(0);
         x1h[kk] = hhi1 ? __ldg(xin + c + dhi1) : T(0);
         dd[kk] = __ldg(wd + c);
         bb[kk] = __ldg(b + c);
@@ -452,7 +590,7 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_smooth_zm(const Op<T> A, const
         off += w1l[kk] * x1l[kk];
         if (hhi1) off += w1h[kk] * x1h[kk];
         off += wz[kk] * xz[kk];
-        if (hz) off += wz[kk + 1] * xz[kk + 2];
+        if (hz) off += pz[kk] * xz[kk + 2];
         xout[c0 + (long long)kk * nxy] = jacobi_update(xz[kk + 1], bb[kk], dd[kk], A.scale, off, omega);
     }
 }
@@ -464,6 +602,7 @@ constexpr int COARSE_BLOCK = 1024;
 template <typename T>
 __global__ void __launch_bounds__(COARSE_BLOCK) k_mg_coarse(const Op<T> A, const T* __restrict__ b,
                                                             T* x, T* xt, T omega, int sweeps) {
+    if (skipped(A.skip)) return;
     T* buf[2] = {x, xt};
     for (int s = 0; s < sweeps; ++s) {
         const T* xin = buf[(s + 1) & 1];
@@ -487,16 +626,19 @@ __global__ void __launch_bounds__(COARSE_BLOCK) k_mg_coarse(const Op<T> A, const
 // transpose of the injection prolongation scaled by 1/8 (a parent with fewer than 8 children,
 // at an odd extent, keeps the factor, so that the cycle stays symmetric).
 //
-// FP64: with (A x)_c = loc_c x_c + scale sum_faces W (x_c - x_nb), the faces between two
-// children of the parent cancel in the sum, so only the faces to cells outside the parent are
-// evaluated; this halves the FP64 arithmetic that bounds the FP64 instance.  FP32: the residual
-// of each child from its full row, which measured faster at 256^3 (16.2 against 18.8 ms per
-// step, where the outside-face form took FP64 from 48.0 down to 41.9 ms).
+// FP64 and symmetric: with (A x)_c = loc_c x_c + scale sum_faces W (x_c - x_nb), the faces
+// between two children of the parent cancel in the sum, so only the faces to cells outside the
+// parent are evaluated; this halves the FP64 arithmetic that bounds the FP64 instance.  (For a
+// non-symmetric operator the two rows of an inner face carry W and Wp, which do not cancel.)
+// Otherwise the residual of each child from its full row, which for FP32 also measured faster
+// at 256^3 (16.2 against 18.8 ms per step, where the outside-face form took FP64 from 48.0 down
+// to 41.9 ms).
 template <typename T>
 __global__ void __launch_bounds__(LIN_BLOCK) k_mg_restrict(const Op<T> A, const T* __restrict__ b,
                                                            const T* __restrict__ x, int cnx,
                                                            int cny, int cnz, FastDiv fcx,
                                                            FastDiv fcxy, T* __restrict__ bc) {
+    if (skipped(A.skip)) return;
     const long long Nc = (long long)cnx * cny * cnz;
     const long long sz = (long long)A.nx * A.ny;
     const int n[3] = {A.nx, A.ny, A.nz};
@@ -506,7 +648,8 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_restrict(const Op<T> A, const 
         int I, J, K;
         coords_fd(cc, fcx, fcxy, I, J, K);
         T acc = T(0);
-        if constexpr (sizeof(T) == 8) {
+        const bool inner_cancel = sizeof(T) == 8 && A.loc && A.Wp[0] == A.W[0];
+        if (inner_cancel) {
 #pragma unroll
             for (int dk = 0; dk < 2; ++dk) {
 #pragma unroll
@@ -563,7 +706,9 @@ template <typename T>
 __global__ void __launch_bounds__(LIN_BLOCK) k_mg_prolong(int nx, int ny, int nz, int cnx, int cny,
                                                           FastDiv fx, FastDiv fxy,
                                                           const T* __restrict__ xc,
-                                                          T* __restrict__ xf) {
+                                                          T* __restrict__ xf,
+                                                          const double* skip) {
+    if (skipped(skip)) return;
     const long long N = (long long)nx * ny * nz;
     for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
          c += (long long)gridDim.x * LIN_BLOCK) {
@@ -574,15 +719,19 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_prolong(int nx, int ny, int nz
 }
 
 // Coarse operator by re-discretisation: local diagonal = mean of the children's local
-// diagonals (diag - scale * sum of their six faces); lower-face coefficient of the coarse
-// cell = (mean of the existing fine lower faces of its first-layer children) / 4.
-// Writes diag_c = local part only; k_mg_diag_faces adds the face sums.
+// diagonals (diag - scale * the six couplings of their rows); each face array of the coarse
+// cell's lower face = (mean of that array over the existing fine lower faces of its first-layer
+// children) / 4, W from W and, for a non-symmetric operator, Wp from Wp (wpc null: symmetric).
+// Writes diag_c = local part only; k_mg_diag_faces adds the row's couplings.
 template <typename TF, typename TC>
 __global__ void __launch_bounds__(LIN_BLOCK) k_mg_coarsen(const Op<TF> A, int cnx, int cny,
                                                           int cnz, TC* __restrict__ dc,
                                                           TC* __restrict__ wcx,
                                                           TC* __restrict__ wcy,
-                                                          TC* __restrict__ wcz) {
+                                                          TC* __restrict__ wcz,
+                                                          TC* __restrict__ wpcx,
+                                                          TC* __restrict__ wpcy,
+                                                          TC* __restrict__ wpcz) {
     const long long Nc = (long long)cnx * cny * cnz;
     const long long sz = (long long)A.nx * A.ny;
     for (long long cc = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; cc < Nc;
@@ -590,8 +739,8 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_coarsen(const Op<TF> A, int cn
         const int K = (int)(cc / ((long long)cnx * cny));
         const long long rem = cc - (long long)K * cnx * cny;
         const int J = (int)(rem / cnx), I = (int)(rem - (long long)J * cnx);
-        double dl = 0.0, wx = 0.0, wy = 0.0, wz = 0.0;
-        int cnt = 0, nxf = 0, nyf = 0, nzf = 0;
+        double dl = 0.0, wl[3] = {0.0, 0.0, 0.0}, wp[3] = {0.0, 0.0, 0.0};
+        int cnt = 0, nf[3] = {0, 0, 0};
         for (int dk = 0; dk < 2; ++dk) {
             const int k = 2 * K + dk;
             if (k >= A.nz) continue;
@@ -602,34 +751,42 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_coarsen(const Op<TF> A, int cn
                     const int i = 2 * I + di;
                     if (i >= A.nx) continue;
                     const long long c = i + (long long)A.nx * (j + (long long)A.ny * k);
-                    // six face coefficients of the child
+                    // the six couplings of the child's row
                     double fsum = 0.0;
                     const int q[3] = {i, j, k};
                     const int n[3] = {A.nx, A.ny, A.nz};
                     const long long s[3] = {1, A.nx, sz};
+                    const int d[3] = {di, dj, dk};
 #pragma unroll
                     for (int ax = 0; ax < 3; ++ax) {
                         fsum += (double)A.W[ax][c];
-                        if (q[ax] < n[ax] - 1) fsum += (double)A.W[ax][c + s[ax]];
-                        else if (A.per[ax]) fsum += (double)A.W[ax][c - (long long)(n[ax] - 1) * s[ax]];
+                        if (q[ax] < n[ax] - 1) fsum += (double)A.Wp[ax][c + s[ax]];
+                        else if (A.per[ax]) fsum += (double)A.Wp[ax][c - (long long)(n[ax] - 1) * s[ax]];
+                        if (d[ax] == 0) {
+                            wl[ax] += (double)A.W[ax][c];
+                            wp[ax] += (double)A.Wp[ax][c];
+                            ++nf[ax];
+                        }
                     }
                     dl += (double)A.diag[c] - (double)A.scale * fsum;
                     ++cnt;
-                    if (di == 0) { wx += (double)A.W[0][c]; ++nxf; }
-                    if (dj == 0) { wy += (double)A.W[1][c]; ++nyf; }
-                    if (dk == 0) { wz += (double)A.W[2][c]; ++nzf; }
                 }
             }
         }
         const double sc = (double)A.scale * 0.25;
         dc[cc] = (TC)(dl / cnt);
-        wcx[cc] = (TC)(sc * wx / nxf);
-        wcy[cc] = (TC)(sc * wy / nyf);
-        wcz[cc] = (TC)(sc * wz / nzf);
+        wcx[cc] = (TC)(sc * wl[0] / nf[0]);
+        wcy[cc] = (TC)(sc * wl[1] / nf[1]);
+        wcz[cc] = (TC)(sc * wl[2] / nf[2]);
+        if (wpcx) {
+            wpcx[cc] = (TC)(sc * wp[0] / nf[0]);
+            wpcy[cc] = (TC)(sc * wp[1] / nf[1]);
+            wpcz[cc] = (TC)(sc * wp[2] / nf[2]);
+        }
     }
 }
 
-// diag += sum of the six face coefficients (scale 1 on coarse levels)
+// diag += sum of the six couplings of the row (scale 1 on coarse levels)
 template <typename T>
 __global__ void __launch_bounds__(LIN_BLOCK) k_mg_diag_faces(Op<T> A, T* __restrict__ diag) {
     const long long sz = (long long)A.nx * A.ny;
@@ -644,29 +801,38 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_diag_faces(Op<T> A, T* __restr
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
             f += A.W[ax][c];
-            if (q[ax] < n[ax] - 1) f += A.W[ax][c + s[ax]];
-            else if (A.per[ax]) f += A.W[ax][c - (long long)(n[ax] - 1) * s[ax]];
+            if (q[ax] < n[ax] - 1) f += A.Wp[ax][c + s[ax]];
+            else if (A.per[ax]) f += A.Wp[ax][c - (long long)(n[ax] - 1) * s[ax]];
         }
         diag[c] += f;
     }
 }
 
-// FP32 copy of the finest operator with the scale folded into the faces
+// FP32 copy of the finest operator with the scale folded into the faces (W and, when the
+// operator is non-symmetric, Wp)
 __global__ void __launch_bounds__(LIN_BLOCK) k_cast_op(const Op<double> A, float* __restrict__ d,
                                                        float* __restrict__ wx,
                                                        float* __restrict__ wy,
-                                                       float* __restrict__ wz) {
+                                                       float* __restrict__ wz,
+                                                       float* __restrict__ px,
+                                                       float* __restrict__ py,
+                                                       float* __restrict__ pz) {
     for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < A.N;
          c += (long long)gridDim.x * LIN_BLOCK) {
         d[c] = (float)A.diag[c];
         wx[c] = (float)(A.scale * A.W[0][c]);
         wy[c] = (float)(A.scale * A.W[1][c]);
         wz[c] = (float)(A.scale * A.W[2][c]);
+        if (px) {
+            px[c] = (float)(A.scale * A.Wp[0][c]);
+            py[c] = (float)(A.scale * A.Wp[1][c]);
+            pz[c] = (float)(A.scale * A.Wp[2][c]);
+        }
     }
 }
 
-// wid = omega / diag and, where loc is given, loc = diag - scale * (sum of the six face
-// coefficients), in TF
+// wid = omega / diag and, where loc is given, loc = diag - scale * (sum of the six couplings of
+// the row), in TF
 template <typename TF, typename TO>
 __global__ void __launch_bounds__(LIN_BLOCK) k_mg_level_prep(const Op<TF> A, double omega,
                                                              TO* __restrict__ wid,
@@ -686,8 +852,8 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_level_prep(const Op<TF> A, dou
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
                 f += A.W[ax][c];
-                if (q[ax] < n[ax] - 1) f += A.W[ax][c + s[ax]];
-                else if (A.per[ax]) f += A.W[ax][c - (long long)(n[ax] - 1) * s[ax]];
+                if (q[ax] < n[ax] - 1) f += A.Wp[ax][c + s[ax]];
+                else if (A.per[ax]) f += A.Wp[ax][c - (long long)(n[ax] - 1) * s[ax]];
             }
             loc[c] = (TO)(d - A.scale * f);
         }
@@ -695,7 +861,8 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_level_prep(const Op<TF> A, dou
 }
 
 __global__ void __launch_bounds__(LIN_BLOCK) k_to_f32(long long N, const double* __restrict__ a,
-                                                      float* __restrict__ b) {
+                                                      float* __restrict__ b, const double* skip) {
+    if (skipped(skip)) return;
     for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
          c += (long long)gridDim.x * LIN_BLOCK)
         b[c] = (float)a[c];
@@ -752,7 +919,7 @@ cudaError_t LinLaunch::jacobi_dot(long long N, const double* r, const double* di
                                   double* part, int& nparts) {
     nparts = stream_blocks(N);
     begin("precond_jacobi");
-    k_jacobi_dot<<<nparts, LIN_BLOCK, 0, st>>>(N, r, diag, z, part);
+    k_jacobi_dot<<<nparts, LIN_BLOCK, 0, st>>>(N, r, diag, z, part, skip);
     return end();
 }
 cudaError_t LinLaunch::dot(long long N, const double* a, const double* b, double* part,
@@ -771,7 +938,31 @@ cudaError_t LinLaunch::cg_init(long long N, const double* b, double* r, double* 
 }
 cudaError_t LinLaunch::reduce(const double* part, int n, double* scal, int op, int slot) {
     begin("reduce");
-    k_reduce<<<1, RED_BLOCK, 0, st>>>(part, n, scal, op, slot);
+    k_reduce<<<1, RED_BLOCK, 0, st>>>(part, n, scal, op, slot, skip);
+    return end();
+}
+cudaError_t LinLaunch::reduce_loop(const double* part, int n, double* scal, int op,
+                                   unsigned long long cond) {
+    begin("reduce");
+    k_reduce_loop<<<1, RED_BLOCK, 0, st>>>(part, n, scal, op, cond);
+    return end();
+}
+cudaError_t LinLaunch::bicg_xr_loop(long long N, const double* scal, double* x, const double* ph,
+                                    const double* sh, const double* s, const double* t,
+                                    double* r, const double* rh, double* part, int& nparts) {
+    nparts = stream_blocks(N);
+    begin("bicg_update_xr");
+    k_bicg_xr_loop<<<nparts, LIN_BLOCK, 0, st>>>(N, scal, x, ph, sh, s, t, r, rh, part);
+    return end();
+}
+cudaError_t LinLaunch::from_f32(long long N, const float* x, double* z) {
+    begin("mg_from_f32");
+    k_from_f32<<<stream_blocks(N), LIN_BLOCK, 0, st>>>(N, x, z, skip);
+    return end();
+}
+cudaError_t LinLaunch::copy(long long N, const double* a, double* b) {
+    begin("copy");
+    k_copy<<<stream_blocks(N), LIN_BLOCK, 0, st>>>(N, a, b, skip);
     return end();
 }
 
@@ -779,8 +970,10 @@ cudaError_t LinLaunch::matvec_ns(const OpNS& A, const double* x, double* y, cons
                                  int two_dots, double* part, int& nparts) {
     nparts = stream_blocks(A.N);
     begin("bicg_matvec");
-    if (two_dots) k_matvec_ns<true><<<nparts, LIN_BLOCK, 0, st>>>(A, x, y, w1, part);
-    else k_matvec_ns<false><<<nparts, LIN_BLOCK, 0, st>>>(A, x, y, w1, part);
+    OpNS B = A;
+    B.skip = skip;
+    if (two_dots) k_matvec_ns<true><<<nparts, LIN_BLOCK, 0, st>>>(B, x, y, w1, part);
+    else k_matvec_ns<false><<<nparts, LIN_BLOCK, 0, st>>>(B, x, y, w1, part);
     return end();
 }
 cudaError_t LinLaunch::bicg_init(long long N, const double* b, double* r, double* rh, double* x,
@@ -820,46 +1013,59 @@ cudaError_t LinLaunch::axpy(long long N, const double* scal, int slot, const dou
 template <typename T>
 cudaError_t LinLaunch::smooth(const Op<T>& A, const T* b, const T* xin, T* xout, T omega,
                               int first) {
-    if (A.N == fine_N) begin(sizeof(T) == 4 ? "mg_smooth_f32_fine" : "mg_smooth_f64_fine");
+    // the finest level's sweeps get their own names (the first sweep of a cycle, from x = 0,
+    // reads only b and omega / diag)
+    if (A.N == fine_N && first) begin(sizeof(T) == 4 ? "mg_smooth_f32_fine_first" : "mg_smooth_f64_fine_first");
+    else if (A.N == fine_N) begin(sizeof(T) == 4 ? "mg_smooth_f32_fine" : "mg_smooth_f64_fine");
     else begin(sizeof(T) == 4 ? "mg_smooth_f32" : "mg_smooth_f64");
     const long long nxy = (long long)A.nx * A.ny;
+    Op<T> B = A;
+    B.skip = skip;
     // (FP32 only: the FP64 sweep is bound by its FP64 arithmetic, not by load latency, and
     // its z-marching form measured slower)
     if (sizeof(T) == 4 && !first && A.nz % ZM == 0 && nxy >= 4 * LIN_BLOCK && xin != xout) {
         const dim3 g((unsigned)((nxy + LIN_BLOCK - 1) / LIN_BLOCK), (unsigned)((A.nz + ZM - 1) / ZM));
-        k_mg_smooth_zm<T><<<g, LIN_BLOCK, 0, st>>>(A, b, xin, xout, omega);
+        k_mg_smooth_zm<T><<<g, LIN_BLOCK, 0, st>>>(B, b, xin, xout, omega);
     } else {
-        k_mg_smooth<T><<<stream_blocks(A.N), LIN_BLOCK, 0, st>>>(A, b, xin, xout, omega, first);
+        k_mg_smooth<T><<<stream_blocks(A.N), LIN_BLOCK, 0, st>>>(B, b, xin, xout, omega, first);
     }
     return end();
 }
 template <typename T>
 cudaError_t LinLaunch::coarse_solve(const Op<T>& A, const T* b, T* x, T* xt, T omega, int sweeps) {
     begin(sizeof(T) == 4 ? "mg_coarse_f32" : "mg_coarse_f64");
-    k_mg_coarse<T><<<1, COARSE_BLOCK, 0, st>>>(A, b, x, xt, omega, sweeps);
+    Op<T> B = A;
+    B.skip = skip;
+    k_mg_coarse<T><<<1, COARSE_BLOCK, 0, st>>>(B, b, x, xt, omega, sweeps);
     return end();
 }
 template <typename T>
 cudaError_t LinLaunch::restrict_res(const Op<T>& A, const T* b, const T* x, int cnx, int cny,
                                     int cnz, T* bc) {
-    begin(sizeof(T) == 4 ? "mg_restrict_f32" : "mg_restrict_f64");
+    if (A.N == fine_N) begin(sizeof(T) == 4 ? "mg_restrict_f32_fine" : "mg_restrict_f64_fine");
+    else begin(sizeof(T) == 4 ? "mg_restrict_f32" : "mg_restrict_f64");
+    Op<T> B = A;
+    B.skip = skip;
     k_mg_restrict<T><<<stream_blocks((long long)cnx * cny * cnz), LIN_BLOCK, 0, st>>>(
-        A, b, x, cnx, cny, cnz, make_fastdiv((unsigned)cnx), make_fastdiv((unsigned)cnx * cny), bc);
+        B, b, x, cnx, cny, cnz, make_fastdiv((unsigned)cnx), make_fastdiv((unsigned)cnx * cny), bc);
     return end();
 }
 template <typename T>
 cudaError_t LinLaunch::prolong(int nx, int ny, int nz, int cnx, int cny, const T* xc, T* xf) {
-    begin(sizeof(T) == 4 ? "mg_prolong_f32" : "mg_prolong_f64");
+    if ((long long)nx * ny * nz == fine_N) begin(sizeof(T) == 4 ? "mg_prolong_f32_fine" : "mg_prolong_f64_fine");
+    else begin(sizeof(T) == 4 ? "mg_prolong_f32" : "mg_prolong_f64");
     k_mg_prolong<T><<<stream_blocks((long long)nx * ny * nz), LIN_BLOCK, 0, st>>>(
-        nx, ny, nz, cnx, cny, make_fastdiv((unsigned)nx), make_fastdiv((unsigned)nx * ny), xc, xf);
+        nx, ny, nz, cnx, cny, make_fastdiv((unsigned)nx), make_fastdiv((unsigned)nx * ny), xc, xf,
+        skip);
     return end();
 }
 template <typename TF, typename TC>
-cudaError_t LinLaunch::coarsen(const Op<TF>& A, int cnx, int cny, int cnz, TC* dc, TC* wx,
-                               TC* wy, TC* wz) {
+cudaError_t LinLaunch::coarsen(const Op<TF>& A, int cnx, int cny, int cnz, TC* dc, TC* const* wc,
+                               TC* const* wpc) {
     begin("mg_coarsen");
     k_mg_coarsen<TF, TC><<<stream_blocks((long long)cnx * cny * cnz), LIN_BLOCK, 0, st>>>(
-        A, cnx, cny, cnz, dc, wx, wy, wz);
+        A, cnx, cny, cnz, dc, wc[0], wc[1], wc[2], wpc ? wpc[0] : nullptr,
+        wpc ? wpc[1] : nullptr, wpc ? wpc[2] : nullptr);
     return end();
 }
 template <typename T>
@@ -874,14 +1080,17 @@ cudaError_t LinLaunch::level_prep(const Op<TF>& A, double omega, TO* wid, TO* lo
     k_mg_level_prep<TF, TO><<<stream_blocks(A.N), LIN_BLOCK, 0, st>>>(A, omega, wid, loc);
     return end();
 }
-cudaError_t LinLaunch::cast_op(const Op<double>& A, float* d, float* wx, float* wy, float* wz) {
+cudaError_t LinLaunch::cast_op(const Op<double>& A, float* d, float* const* w, float* const* wp) {
     begin("mg_cast_op");
-    k_cast_op<<<stream_blocks(A.N), LIN_BLOCK, 0, st>>>(A, d, wx, wy, wz);
+    k_cast_op<<<stream_blocks(A.N), LIN_BLOCK, 0, st>>>(A, d, w[0], w[1], w[2],
+                                                        wp ? wp[0] : nullptr,
+                                                        wp ? wp[1] : nullptr,
+                                                        wp ? wp[2] : nullptr);
     return end();
 }
 cudaError_t LinLaunch::to_f32(long long N, const double* a, float* b) {
     begin("mg_to_f32");
-    k_to_f32<<<stream_blocks(N), LIN_BLOCK, 0, st>>>(N, a, b);
+    k_to_f32<<<stream_blocks(N), LIN_BLOCK, 0, st>>>(N, a, b, skip);
     return end();
 }
 cudaError_t LinLaunch::from_f32_dot(long long N, const float* x, const double* r, double* z,
@@ -907,11 +1116,11 @@ template cudaError_t LinLaunch::restrict_res<float>(const Op<float>&, const floa
 template cudaError_t LinLaunch::prolong<double>(int, int, int, int, int, const double*, double*);
 template cudaError_t LinLaunch::prolong<float>(int, int, int, int, int, const float*, float*);
 template cudaError_t LinLaunch::coarsen<double, double>(const Op<double>&, int, int, int, double*,
-                                                        double*, double*, double*);
+                                                        double* const*, double* const*);
 template cudaError_t LinLaunch::coarsen<double, float>(const Op<double>&, int, int, int, float*,
-                                                       float*, float*, float*);
+                                                       float* const*, float* const*);
 template cudaError_t LinLaunch::coarsen<float, float>(const Op<float>&, int, int, int, float*,
-                                                      float*, float*, float*);
+                                                      float* const*, float* const*);
 template cudaError_t LinLaunch::diag_faces<double>(const Op<double>&, double*);
 template cudaError_t LinLaunch::diag_faces<float>(const Op<float>&, float*);
 template cudaError_t LinLaunch::level_prep<double, double>(const Op<double>&, double, double*,

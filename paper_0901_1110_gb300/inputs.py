@@ -163,8 +163,12 @@ def lognormal_hhe(shape=(128, 128, 128), box=1.0 * MPC, seed=0, nbar=1e-3, sigma
 
 def config_uniform_32():
     """Plain FP64 method: 32^3, 1 Mpc, H only, n_H = 1e-3, T0 = 100 K, x_HII = 1e-4, one
-    central 5e48 s^-1 source at 13.6 eV, zero-flux boundaries, a = 1, 5 steps of 1e12 s."""
-    return uniform_h(32, name="uniform_h_32")
+    central 5e48 s^-1 source at 13.6 eV, zero-flux boundaries, a = 1, 5 steps of 1e12 s.
+    theta = 1: the set-up leaves theta open, and with c kappa dt = 189 in the neutral gas the
+    theta = 0.51 step has no positive solution ((1 - theta) c kappa dt > 1 drives E below 0)."""
+    w = uniform_h(32, name="uniform_h_32")
+    w.theta = 1.0
+    return w
 
 
 # Radiation scaling u_E of the source-driven lognormal runs: a round number of the order of the
@@ -229,6 +233,39 @@ def config_cosmo(n=512, nsrc=256, seed=0, box=1.0 * MPC, z0=10.0, z1=6.0, nsteps
     a = flat_lcdm_a(mids)
     w.schedule = [(float(dt), float(ai), float(flat_lcdm_adot(ai))) for ai in a]
     return w
+
+
+# the cosmological I-front (the Shapiro-Giroux set-up) -------------------------------------------
+
+# (q0, z_i) -> (H0 in 100 km/s/Mpc, Omega_m, initial baryon density g cm^-3, initial proper box kpc)
+SG_CASES = {(0.5, 4.0): (0.5, 1.0, 1.175e-28, 80.0), (0.05, 4.0): (1.0, 0.1, 2.35e-28, 60.0),
+            (0.5, 10.0): (0.5, 1.0, 1.175e-28, 36.0), (0.05, 10.0): (1.0, 0.1, 2.35e-28, 27.0)}
+
+
+def config_sg(n=32, q0=0.5, z_i=4.0, ndot=5e48, T=1e4, E0_proper=1e-35):
+    """Hydrogen of uniform comoving density around a 13.6 eV source in a matter-only universe
+    of deceleration parameter q0, from redshift z_i: the four parameter sets of the
+    cosmological radiative-ionization test (initial box and baryon density as listed there),
+    T = 1e4 K held, neutral gas (x_HII = 0), E = 1e-35 erg cm^-3 proper.  The source sits in
+    the corner cell of one octant (reflecting faces), which therefore emits ndot / 8.  Scale
+    factors a = 1 / (1 + z); densities and E are comoving (proper times a^3); dx is comoving."""
+    h, om, rho_i, box_kpc = SG_CASES[(q0, z_i)]
+    a_i = 1.0 / (1.0 + z_i)
+    nH_i = rho_i / _MH                                   # proper, hydrogen only
+    w = uniform_h(n, box=box_kpc * KPC / a_i, nH=nH_i * a_i ** 3, T0=T, x0=0.0,
+                  E0=E0_proper * a_i ** 3, ndot=ndot / 8.0, source="corner",
+                  name=f"sg_q{q0}_z{z_i}_{n}")
+    w.theta = 1.0
+    w.u_E = 1e-20
+    w.meta.update(q0=q0, z_i=z_i, a_i=a_i, H0=h * 100e5 / MPC, omega_m=om, nH_i=nH_i,
+                  ndot=ndot)
+    return w
+
+
+def matter_only_adot(a, H0, omega_m):
+    """da/dt of a universe with matter and curvature only: a H0 sqrt(Om a^-3 + (1 - Om) a^-2)."""
+    a = np.asarray(a, dtype=np.float64)
+    return a * H0 * np.sqrt(omega_m / a ** 3 + (1.0 - omega_m) / a ** 2)
 
 
 # LTE coupling: matter-radiation equilibration (the Turner-Stone set-up) ---------------------------

@@ -7,7 +7,7 @@ import pytest
 from conftest import oracle_problem
 from oracle import closure as cl, solve as sv
 from paper_0901_1110_gb300 import inputs
-from parity import field_errors
+from parity import TIGHT_NEWTON_TOL, field_errors
 
 pytestmark = pytest.mark.gpu
 KPC = inputs.KPC
@@ -27,7 +27,7 @@ def rhi():
 
 def _close(g, ref, w, keys):
     """Per-element bound 1e-10 on E, e and (ionization model) every species fraction."""
-    err = field_errors(g, ref, w.nH, w.y_he, keys=keys)
+    err = field_errors(g, ref, w.nH, w.y_he, keys=keys, scales=(w.u_e, w.u_n, w.u_E))
     assert max(err.values()) <= 1e-10, err
 
 
@@ -42,8 +42,8 @@ def test_ionization_steps_with_dirichlet_faces_match_oracle(rhi, ljac):
     p = oracle_problem(w)
     ref = w.state()
     for _ in range(3):
-        s.step(w.dt, newton_tol=1e-12, lin_tol=1e-12)
-        ref, info = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, 1e-13, linear="direct")
+        s.step(w.dt, newton_tol=TIGHT_NEWTON_TOL, lin_tol=1e-12)
+        ref, info = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, TIGHT_NEWTON_TOL, linear="direct")
         assert info["converged"]
         _close(s.get_state(), ref, w, ("E", "e"))
 
@@ -56,8 +56,8 @@ def test_lte_steps_with_dirichlet_faces_match_oracle(rhi):
     p = oracle_problem(w)
     ref = w.state()
     for _ in range(3):
-        s.step(w.dt, newton_tol=1e-12, lin_tol=1e-12)
-        ref, info = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, 1e-13, linear="direct")
+        s.step(w.dt, newton_tol=TIGHT_NEWTON_TOL, lin_tol=1e-12)
+        ref, info = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, TIGHT_NEWTON_TOL, linear="direct")
         assert info["converged"]
         _close(s.get_state(), ref, w, ("E", "e"))
 

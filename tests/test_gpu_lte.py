@@ -8,7 +8,7 @@ from scipy.optimize import brentq
 from conftest import oracle_problem
 from oracle import closure as cl, solve as sv
 from paper_0901_1110_gb300 import inputs
-from parity import field_errors
+from parity import TIGHT_NEWTON_TOL, field_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -36,10 +36,10 @@ def test_lte_steps_match_oracle(rhi, ljac, theta):
     p = oracle_problem(w)
     ref = w.state()
     for _ in range(3):
-        s.step(w.dt, newton_tol=1e-12, lin_tol=1e-12)
-        ref, info = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, 1e-13, linear="direct")
+        s.step(w.dt, newton_tol=TIGHT_NEWTON_TOL, lin_tol=1e-12)
+        ref, info = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, TIGHT_NEWTON_TOL, linear="direct")
         assert info["converged"]
-        err = field_errors(s.get_state(), ref, w.nH)
+        err = field_errors(s.get_state(), ref, w.nH, scales=(w.u_e, w.u_n, w.u_E))
         assert max(err.values()) <= 1e-10, err
 
 

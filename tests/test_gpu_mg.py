@@ -40,7 +40,10 @@ TOL = {"fp64": 1e-12, "fp32": 1e-4}
 
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_vcycle_matches_numpy_restatement(rhi, case, precision):
+@pytest.mark.parametrize("matrix", ["lagged", "newton"])
+def test_vcycle_matches_numpy_restatement(rhi, case, precision, matrix):
+    """The hierarchy of the lagged-D matrix (symmetric), and that of the exact Newton matrix
+    (non-symmetric: its faces carry both couplings, Wp from the exported upper entries)."""
     c = CASES[case]
     w = inputs.lognormal_hhe(c["shape"], box=200 * KPC, nsrc=3, dt=5e12, nsteps=2,
                              bc=c["bc"], seed=c["seed"])
@@ -51,7 +54,8 @@ def test_vcycle_matches_numpy_restatement(rhi, case, precision):
     omega, pre, post, coarse = 0.9, 2, 2, 16
     s = rhi.solver_for_workload(w, precond=code, mg_levels=c["levels"], mg_pre=pre,
                                 mg_post=post, mg_coarse_sweeps=coarse, mg_omega=omega,
-                                limiter_jacobian=0, vcycle_graph=0)
+                                limiter_jacobian=0 if matrix == "lagged" else 2, mg_matrix=1,
+                                vcycle_graph=0)
     # a step first, so that the operator carries an ionised region around the sources
     s.step(w.dt, newton_tol=1e-9, lin_tol=1e-10)
     lin = s.linearize(w.dt)
@@ -59,8 +63,13 @@ def test_vcycle_matches_numpy_restatement(rhi, case, precision):
     z = s.precond_apply(r)
     s.close()
     shape = (nz, ny, nx)
-    ops = mgr.hierarchy(lin["diag"].reshape(shape),
-                        [lin["face"][ax].reshape(shape) for ax in range(3)], c["levels"])
+    W = [lin["face"][ax].reshape(shape) for ax in range(3)]
+    Wp = None
+    if matrix == "newton":
+        # row c's coupling to its upper neighbour sits, per face, at the upper cell
+        Wp = [np.roll(lin["face_hi"][ax].reshape(shape), 1, axis=2 - ax) for ax in range(3)]
+        assert max(np.abs(Wp[ax] - W[ax]).max() for ax in range(3)) > 1e-6 * np.abs(W[0]).max()
+    ops = mgr.hierarchy(lin["diag"].reshape(shape), W, c["levels"], Wp)
     assert len(ops) == c["levels"]
     zr = mgr.vcycle(ops, r.reshape(shape), omega, pre, post, coarse).ravel()
     rel = np.linalg.norm(z - zr) / np.linalg.norm(zr)

@@ -7,7 +7,7 @@ import pytest
 from conftest import oracle_problem
 from oracle import mlp as om, model as md, solve as sv
 from paper_0901_1110_gb300 import inputs
-from parity import field_errors
+from parity import TIGHT_NEWTON_TOL, field_errors
 
 pytestmark = pytest.mark.gpu
 KPC = inputs.KPC
@@ -167,13 +167,13 @@ def test_learned_guess_reaches_the_same_root(rhi, trained):
     ref = w.state()
     used = []
     for _ in range(2):
-        s.step(w.dt, newton_tol=1e-12, lin_tol=1e-12)
+        s.step(w.dt, newton_tol=TIGHT_NEWTON_TOL, lin_tol=1e-12)
         st = s.stats()
         used.append(st["guess_used"])
         assert st["res_guess_prev"] > 0
-        ref, info = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, 1e-13, linear="direct")
+        ref, info = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, TIGHT_NEWTON_TOL, linear="direct")
         assert info["converged"]
-        err = field_errors(s.get_state(), ref, w.nH, w.y_he)
+        err = field_errors(s.get_state(), ref, w.nH, w.y_he, scales=(w.u_e, w.u_n, w.u_E))
         assert max(err.values()) <= 1e-10, err
     assert rhi.RHI_GUESS_LEARNED in used, used
 
@@ -231,11 +231,11 @@ def test_learned_start_restart_reaches_the_same_root(rhi, trained):
     w = trained["workload"]
     s = rhi.solver_for_workload(w, guess=rhi.RHI_GUESS_LEARNED, mlp_restart=1)
     s.mlp_set_weights(trained["w"])
-    s.step(w.dt, newton_tol=1e-12, lin_tol=1e-12)
+    s.step(w.dt, newton_tol=TIGHT_NEWTON_TOL, lin_tol=1e-12)
     st = s.stats()
     p = oracle_problem(w)
-    ref, info = sv.implicit_step(p, w.state(), w.dt, 1.0, 0.0, 1e-13, linear="direct")
-    err = field_errors(s.get_state(), ref, w.nH, w.y_he)
+    ref, info = sv.implicit_step(p, w.state(), w.dt, 1.0, 0.0, TIGHT_NEWTON_TOL, linear="direct")
+    err = field_errors(s.get_state(), ref, w.nH, w.y_he, scales=(w.u_e, w.u_n, w.u_E))
     assert max(err.values()) <= 1e-10, err
     if st["guess_restarts"]:
         assert st["guess_used"] == rhi.RHI_GUESS_PREVIOUS

@@ -5,7 +5,7 @@ import pytest
 from conftest import oracle_problem
 from oracle import closure as cl, model as md, solve as sv
 from paper_0901_1110_gb300 import inputs
-from parity import field_errors
+from parity import TIGHT_NEWTON_TOL, field_errors
 
 pytestmark = pytest.mark.gpu
 KPC = inputs.KPC
@@ -27,7 +27,7 @@ def rhi():
 
 
 def _field_errors(gpu, ref, w, mask=None):
-    return field_errors(gpu, ref, w.nH, w.y_he, mask=mask)
+    return field_errors(gpu, ref, w.nH, w.y_he, mask=mask, scales=(w.u_e, w.u_n, w.u_E))
 
 
 def _workloads():
@@ -115,8 +115,8 @@ def test_steps_match_oracle(rhi, name, precond):
     p = oracle_problem(w)
     ref = w.state()
     for step in range(w.nsteps):
-        s.step(w.dt, 1.0, 0.0, newton_tol=1e-12, lin_tol=1e-12)
-        ref, stats = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, 1e-13, linear="direct")
+        s.step(w.dt, 1.0, 0.0, newton_tol=TIGHT_NEWTON_TOL, lin_tol=1e-12)
+        ref, stats = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, TIGHT_NEWTON_TOL, linear="direct")
         assert stats["converged"]
         err = _field_errors(s.get_state(), ref, w)
         assert max(err.values()) <= TOL_FP64, (step, err, s.stats())
@@ -133,8 +133,8 @@ def test_steps_with_dD_dE_match_oracle(rhi, name, ljac):
     p = oracle_problem(w)
     ref = w.state()
     for step in range(w.nsteps):
-        s.step(w.dt, 1.0, 0.0, newton_tol=1e-12, lin_tol=1e-12)
-        ref, stats = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, 1e-13, linear="direct")
+        s.step(w.dt, 1.0, 0.0, newton_tol=TIGHT_NEWTON_TOL, lin_tol=1e-12)
+        ref, stats = sv.implicit_step(p, ref, w.dt, 1.0, 0.0, TIGHT_NEWTON_TOL, linear="direct")
         err = _field_errors(s.get_state(), ref, w)
         assert max(err.values()) <= TOL_FP64, (step, err, s.stats())
 
@@ -143,9 +143,9 @@ def test_predictor_guess_reaches_the_same_root(rhi):
     """Eq. explicit_predictor as the Newton initial guess: same solution as U^n."""
     w = WL["lognormal_hhe"]
     a = rhi.solver_for_workload(w, guess=rhi.RHI_GUESS_PREDICTOR)
-    a.step(w.dt, newton_tol=1e-12, lin_tol=1e-12)
+    a.step(w.dt, newton_tol=TIGHT_NEWTON_TOL, lin_tol=1e-12)
     p = oracle_problem(w)
-    ref, _ = sv.implicit_step(p, w.state(), w.dt, 1.0, 0.0, 1e-13, guess="predictor")
+    ref, _ = sv.implicit_step(p, w.state(), w.dt, 1.0, 0.0, TIGHT_NEWTON_TOL, guess="predictor")
     assert max(_field_errors(a.get_state(), ref, w).values()) <= TOL_FP64
 
 
@@ -159,8 +159,8 @@ def test_isothermal_and_cosmological_terms(rhi):
     p = oracle_problem(w, isothermal=True)
     ref = w.state()
     for _ in range(2):
-        s.step(w.dt, a, adot, newton_tol=1e-12, lin_tol=1e-12)
-        ref, st = sv.implicit_step(p, ref, w.dt, a, adot, 1e-13)
+        s.step(w.dt, a, adot, newton_tol=TIGHT_NEWTON_TOL, lin_tol=1e-12)
+        ref, st = sv.implicit_step(p, ref, w.dt, a, adot, TIGHT_NEWTON_TOL)
         assert st["converged"]
     err = _field_errors(s.get_state(), ref, w)
     assert max(err.values()) <= TOL_FP64, err
@@ -246,11 +246,11 @@ def test_faint_field_matches_oracle(rhi):
     E[: w.nz // 2] *= 1e-180
     w.E = E
     s = rhi.solver_for_workload(w, limiter_jacobian=2)
-    s.step(w.dt, newton_tol=1e-12, lin_tol=1e-12)
+    s.step(w.dt, newton_tol=TIGHT_NEWTON_TOL, lin_tol=1e-12)
     got = s.get_state()
     s.close()
     p = oracle_problem(w)
-    ref, _ = sv.implicit_step(p, w.state(), w.dt, 1.0, 0.0, 1e-13)
+    ref, _ = sv.implicit_step(p, w.state(), w.dt, 1.0, 0.0, TIGHT_NEWTON_TOL)
     Eg = np.asarray(got["E"]).reshape(w.nz, w.ny, w.nx)
     assert np.all(np.isfinite(Eg)) and np.all(Eg > 0)
     err = _field_errors(got, ref, w)
@@ -269,9 +269,9 @@ def test_degenerate_grids(rhi, shape):
     w.theta = 1.0
     w.u_E = 1e-18
     s = rhi.solver_for_workload(w)
-    s.step(w.dt, newton_tol=1e-12, lin_tol=1e-12)
+    s.step(w.dt, newton_tol=TIGHT_NEWTON_TOL, lin_tol=1e-12)
     p = oracle_problem(w)
-    ref, _ = sv.implicit_step(p, w.state(), w.dt, 1.0, 0.0, 1e-13)
+    ref, _ = sv.implicit_step(p, w.state(), w.dt, 1.0, 0.0, TIGHT_NEWTON_TOL)
     assert max(_field_errors(s.get_state(), ref, w).values()) <= TOL_FP64
 
 
@@ -298,3 +298,34 @@ def test_vcycle_graph_matches_direct_launches(rhi):
     for key in ("E", "e", "n"):
         assert np.array_equal(np.asarray(out[0][0][key]), np.asarray(out[1][0][key])), key
     assert np.array_equal(out[0][2], out[1][2])
+
+
+@pytest.mark.parametrize("precond", ["mg32", "mg64"])
+def test_krylov_graph_matches_direct_launches(rhi, precond):
+    """BiCGStab as one CUDA graph launch per solve (a while node whose iterations decide on the
+    device whether to continue) against the same kernels launched from the host with one read
+    per iteration: the steps agree bit for bit, with the same Newton, Krylov and V-cycle
+    counts, also across a change of step size (a new graph).  With the graph a step reads the
+    device once at its start, once per Newton iteration (or line-search trial), and once at
+    its end."""
+    w = WL["lognormal_hhe"]
+    code = {"mg32": rhi.RHI_PRECOND_MG_FP32, "mg64": rhi.RHI_PRECOND_MG_FP64}[precond]
+    out = []
+    for graph in (0, 1):
+        s = rhi.solver_for_workload(w, precond=code, mg_levels=4, limiter_jacobian=2,
+                                    krylov_graph=graph)
+        stats = []
+        for dt in (w.dt, w.dt, 0.5 * w.dt):
+            s.step(dt, newton_tol=1e-10, lin_tol=1e-10)
+            stats.append(s.stats())
+        out.append((s.get_state(), stats))
+        s.close()
+    for key in ("E", "e", "n"):
+        assert np.array_equal(np.asarray(out[0][0][key]), np.asarray(out[1][0][key])), key
+    for a, b in zip(out[0][1], out[1][1]):
+        for k in ("newton_its", "pcg_its", "vcycles", "backtracks", "krylov_fallbacks"):
+            assert a[k] == b[k], (k, a[k], b[k])
+    for st in out[1][1]:
+        assert st["krylov_fallbacks"] == 0
+        assert st["host_syncs"] <= st["newton_its"] + st["backtracks"] + 2, st
+        assert st["host_syncs"] < out[0][1][0]["host_syncs"]

@@ -38,7 +38,9 @@ def _neighbours(shape, periodic, k, j, i):
     return out
 
 
-def _apply_loops(d, W, x, periodic):
+def _apply_loops(d, W, x, periodic, Wp=None):
+    """Row c: d x_c - (its lower face's W) x_lo - (its upper face's Wp) x_hi, per axis."""
+    Wp = W if Wp is None else Wp
     shape = d.shape
     y = np.zeros_like(x)
     for k in range(shape[0]):
@@ -49,9 +51,47 @@ def _apply_loops(d, W, x, periodic):
                     if lo is not None:
                         v -= W[ax][k, j, i] * x[lo]
                     if hi is not None:
-                        v -= W[ax][hi_face] * x[hi]
+                        v -= Wp[ax][hi_face] * x[hi]
                 y[k, j, i] = v
     return y
+
+
+def _coarsen_loops_nonsym(d, W, Wp, periodic):
+    """Coarse operator of a non-symmetric operator from its definition, loop by loop."""
+    shape = d.shape
+    cs = tuple((n + 1) // 2 for n in shape)
+    dc = np.zeros(cs)
+    Wc = [np.zeros(cs) for _ in range(3)]
+    Wpc = [np.zeros(cs) for _ in range(3)]
+    for K, J, I in np.ndindex(*cs):
+        loc, cnt = 0.0, 0
+        fs, fp, fc = [0.0] * 3, [0.0] * 3, [0] * 3
+        for dk, dj, di in np.ndindex(2, 2, 2):
+            k, j, i = 2 * K + dk, 2 * J + dj, 2 * I + di
+            if k >= shape[0] or j >= shape[1] or i >= shape[2]:
+                continue
+            row = 0.0
+            for ax, lo, hi, hi_face in _neighbours(shape, periodic, k, j, i):
+                row += W[ax][k, j, i]
+                if hi is not None:
+                    row += Wp[ax][hi_face]
+            loc += d[k, j, i] - row
+            cnt += 1
+            for ax, first in enumerate((di == 0, dj == 0, dk == 0)):
+                if first:
+                    fs[ax] += W[ax][k, j, i]
+                    fp[ax] += Wp[ax][k, j, i]
+                    fc[ax] += 1
+        dc[K, J, I] = loc / cnt
+        for ax in range(3):
+            Wc[ax][K, J, I] = 0.25 * fs[ax] / fc[ax]
+            Wpc[ax][K, J, I] = 0.25 * fp[ax] / fc[ax]
+    for K, J, I in np.ndindex(*cs):
+        for ax, lo, hi, hi_face in _neighbours(cs, periodic, K, J, I):
+            dc[K, J, I] += Wc[ax][K, J, I]
+            if hi is not None:
+                dc[K, J, I] += Wpc[ax][hi_face]
+    return dc, Wc, Wpc
 
 
 def _coarsen_loops(d, W, periodic):
@@ -152,3 +192,48 @@ def test_vcycle_is_symmetric_positive_and_contracts(periodic, shape):
     for _ in range(10):
         x = x + M(b - mgr.apply(d, W, x))
     assert np.linalg.norm(b - mgr.apply(d, W, x)) < 1e-3 * r0
+
+
+def _random_nonsym(shape, periodic, seed):
+    """Non-symmetric couplings: Wp = W times a factor in [0.5, 1.5], diagonally dominant rows."""
+    d, W = _random_operator(shape, periodic, seed)
+    rng = np.random.default_rng(seed + 100)
+    Wp = [w * rng.uniform(0.5, 1.5, size=shape) for w in W]
+    return d + mgr.face_sum(W, Wp) - mgr.face_sum(W), W, Wp
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_nonsymmetric_apply_matches_loops(periodic):
+    d, W, Wp = _random_nonsym((3, 4, 5), periodic, 7)
+    x = np.random.default_rng(8).standard_normal(d.shape)
+    np.testing.assert_allclose(mgr.apply(d, W, x, Wp), _apply_loops(d, W, x, periodic, Wp),
+                               rtol=1e-13, atol=1e-13)
+    # the symmetric form is the special case Wp = W
+    np.testing.assert_array_equal(mgr.apply(d, W, x, W), mgr.apply(d, W, x))
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("shape", [(4, 6, 8), (5, 6, 7), (1, 3, 2)])
+def test_nonsymmetric_coarsen_matches_loops(periodic, shape):
+    d, W, Wp = _random_nonsym(shape, periodic, 9)
+    cs = mgr.levels(shape, 2)[1]
+    dc, Wc, Wpc = mgr.coarsen(d, W, cs, Wp)
+    dl, Wl, Wpl = _coarsen_loops_nonsym(d, W, Wp, periodic)
+    np.testing.assert_allclose(dc, dl, rtol=1e-13)
+    for ax in range(3):
+        np.testing.assert_allclose(Wc[ax], Wl[ax], rtol=1e-13, atol=1e-15)
+        np.testing.assert_allclose(Wpc[ax], Wpl[ax], rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 8), (6, 7, 9)])
+def test_nonsymmetric_vcycle_contracts(shape):
+    """The cycle of a non-symmetric diagonally dominant operator reduces the residual of
+    x <- x + M (b - A x) as the symmetric one does."""
+    d, W, Wp = _random_nonsym(shape, False, 11)
+    ops = mgr.hierarchy(d, W, 3, Wp)
+    assert all(len(o) == 3 for o in ops)
+    b = np.random.default_rng(12).standard_normal(d.shape)
+    x = np.zeros_like(b)
+    for _ in range(10):
+        x = x + mgr.vcycle(ops, b - mgr.apply(d, W, x, Wp), 0.9, 2, 2, 16)
+    assert np.linalg.norm(b - mgr.apply(d, W, x, Wp)) < 1e-3 * np.linalg.norm(b)

@@ -78,3 +78,32 @@ def test_ifront_helpers():
     aB = cl.rate_formulas(np.array([1e4]))[0, 0]
     rS = (3 * 5e48 / (4 * np.pi * aB * 1e-3 ** 2)) ** (1 / 3) / KPC
     assert rS == pytest.approx(5.4, rel=0.01)
+
+
+@pytest.mark.parametrize("q0,z_i", [(0.5, 4.0), (0.05, 4.0), (0.5, 10.0), (0.05, 10.0)])
+def test_sg_tau_closed_form_is_its_integral(q0, z_i):
+    """Eq. SG-tau with eq. SG-F is the closed form of the recombination depth
+    lambda int_1^a a'^-3 g(a') da' with H0 (1 + z_i) dt = g da (matter and curvature only):
+    quadrature of that definition agrees for the four parameter pairs of the paper."""
+    from scipy import integrate
+    lam = 2.246
+    for a in (1.0, 1.3, 2.0, 5.0, 11.0):
+        q, _ = integrate.quad(lambda x: lam * x ** -3 * ts.sg_g(x, q0, z_i), 1.0, a,
+                              epsabs=0.0, epsrel=1e-13)
+        assert ts.sg_tau(a, lam, q0, z_i) == pytest.approx(q, rel=1e-11, abs=1e-14)
+
+
+def test_sg_ifront_limits():
+    """Eq. SG-solution: at early times photon counting, r_I^3 = r_S,i^3 lam g(1) (a - 1)
+    (no recombinations yet); for fast recombination (lam -> inf) the comoving Stromgren radius
+    of the diluted gas, r_S,i a (r_S proper grows as a^2 with n ~ a^-3); and in between the
+    front lags that Stromgren radius."""
+    q0, z_i = 0.5, 4.0
+    lam = 2.246
+    a = 1.0 + 1e-5
+    r = ts.sg_ifront(a, lam, q0, z_i)[0]
+    assert r ** 3 == pytest.approx(lam * ts.sg_g(1.0, q0, z_i) * 1e-5, rel=1e-4)
+    for a in (1.5, 3.0):
+        assert ts.sg_ifront(a, 1e5, q0, z_i)[0] == pytest.approx(a, rel=1e-3)
+    r = ts.sg_ifront([1.25, 2.5, 5.0], lam, q0, z_i)
+    assert np.all(np.diff(r) > 0) and np.all(r < np.array([1.25, 2.5, 5.0]))
