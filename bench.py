@@ -79,9 +79,9 @@ ALU_FLOPS = {
 }
 # DRAM bytes per launch (read + write) from ncu, per cell of a capture times the cells of the
 # timed grid (each of these kernels streams its fields once, so traffic grows with the cells);
-# an entry is removed when its kernel changes.  The cell kernel's entry (521.9e6 / 128^3) went
-# with the exact rescaling of faint limiter faces, which touched its Dirichlet-face code.
-TRAFFIC_PER_CELL = {}
+# an entry is removed when its kernel changes.  k_cell<3,1> at 128^3: 368.94 MB read +
+# 151.53 MB written per launch (ncu --set full, the current kernel).
+TRAFFIC_PER_CELL = {"cell_residual_schur": (368.936192e6 + 151.531520e6) / 128 ** 3}
 
 FORM_TEXT = {
     "plain_fp64": "FP64 Newton/Schur/BiCGStab + FP64 multigrid V-cycle of the Newton matrix "

@@ -255,24 +255,27 @@ int rhi_advance(rhi_handle h, double t_end, double dt0, double dt_min, double dt
                 int* steps);
 
 /* Learned Newton initial guess (an addition; Sec. 3.2 leaves the initial iterate free): a
-   per-cell MLP 9 -> 64 -> 64 -> 64 -> 6 with SiLU predicting the state at t^{n+1} from the
-   state at t^n.  Features: log10 E/u_E, log10 e/u_e, log10 of the HI, HeI, HeII fractions,
-   log10 n_H/u_n, log10(dt Gamma_HI + 1e-30), log10(1 + 4 pi eta dt / E), log10(dt / 1e12 s).
-   Outputs: log10 E'/E, log10 e'/e, logit of x_HI', logits of the He fractions (softmax).
-   Weights (FP32, RHI_MLP_NWEIGHTS): W1 (64x9, row major), b1 (64), W2 (64x64), b2, W3
-   (64x64), b3, W4 (6x64), b4 (6), then the input normalisation mean (9) and scale (9).
-   Inference uses BF16 copies on the tensor cores with FP32 accumulation; training updates
-   the FP32 weights with Adam using FP32 forward / backward kernels.  With guess =
+   per-cell MLP 13 -> 64 -> 64 -> 64 -> 6 with SiLU predicting the state at t^{n+1} from the
+   state at t^n and its change over the previous step.  Features: log10 E/u_E, log10 e/u_e,
+   log10 of the HI, HeI, HeII fractions, log10 n_H/u_n, log10(dt Gamma_HI + 1e-30),
+   log10(1 + 4 pi eta dt / E), log10(dt / 1e12 s), log10 E/E^{n-1}, log10 e/e^{n-1},
+   logit x_HI - logit x_HI^{n-1}, log10(dt / dt^{n-1}) (the last four 0 before the first
+   step; the library keeps the state before its last accepted step, also across
+   rhi_set_state).  Outputs: log10 E'/E, log10 e'/e, logit of x_HI', logits of the He
+   fractions (softmax).  Weights (FP32, RHI_MLP_NWEIGHTS): W1 (64x13, row major), b1 (64), W2
+   (64x64), b2, W3 (64x64), b3, W4 (6x64), b4 (6), then the input normalisation mean (13) and
+   scale (13).  Inference uses BF16 copies on the tensor cores with FP32 accumulation; training
+   updates the FP32 weights with Adam using FP32 forward / backward kernels.  With guess =
    RHI_GUESS_LEARNED a step evaluates ||f|| at U^n and at the network's guess (cells whose
    predicted changes are all below params.mlp_gate keep U^n) and starts Newton from the
    smaller; rhi_stats.guess_used says which. */
-#define RHI_MLP_IN 9
+#define RHI_MLP_IN 13
 #define RHI_MLP_HID 64
 #define RHI_MLP_OUT 6
-#define RHI_MLP_NWEIGHTS (64 * 9 + 64 + 64 * 64 + 64 + 64 * 64 + 64 + 6 * 64 + 6 + 9 + 9)
+#define RHI_MLP_NWEIGHTS (64 * 13 + 64 + 64 * 64 + 64 + 64 * 64 + 64 + 6 * 64 + 6 + 13 + 13)
 int rhi_mlp_set_weights(rhi_handle h, const float* w, size_t n);
 int rhi_mlp_get_weights(rhi_handle h, float* w, size_t n);
-/* Features (N x 9, FP32) of the current state for a step of length dt at expansion a. */
+/* Features (N x 13, FP32) of the current state for a step of length dt at expansion a. */
 int rhi_mlp_features(rhi_handle h, double dt, double a, float* X, int on_device);
 /* Training targets (N x 6, FP32) of the step from the given earlier state (E, e, n as in
    rhi_set_state) to the current state. */
@@ -283,7 +286,7 @@ int rhi_mlp_targets(rhi_handle h, const double* E_old, const double* e_old,
    decoded (E' = E 10^o0, e' = e 10^o1, x_HI' = 1 / (1 + exp(-o2)), He fractions by softmax of
    o3..o5), cells whose predicted changes all stay below params.mlp_gate keeping U^n. */
 int rhi_mlp_guess(rhi_handle h, double dt, double a, double* U0, int on_device);
-/* Network outputs Y (n x 6) for features X (n x 9) on the tensor cores (BF16 weights). */
+/* Network outputs Y (n x 6) for features X (n x 13) on the tensor cores (BF16 weights). */
 int rhi_mlp_forward(rhi_handle h, const float* X, float* Y, long long n, int on_device);
 /* Mean squared error over the n samples and its gradient wrt the FP32 weights (FP32
    forward / backward; the normalisation entries get 0). */

@@ -4,28 +4,33 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
 Not part of the paper: an added form in which a small network, trained on Newton solutions
 the method itself produces, supplies the Newton initial guess U_0 (Sec. 3.2 leaves U_0 free;
-Sec. 3.2.4 uses an explicit predictor).  The network maps 9 features of a cell at t^n to 6
-outputs that fix the predicted state at t^{n+1}:
+Sec. 3.2.4 uses an explicit predictor).  The network maps 13 features of a cell at t^n (and of
+its change over the previous step t^{n-1} -> t^n) to 6 outputs that fix the predicted state at
+t^{n+1}:
 
   features  f0 = log10(E / u_E)          f1 = log10(e / u_e)       f2 = log10(n_HI / n_H)
             f3 = log10(n_HeI / n_He)     f4 = log10(n_HeII / n_He) f5 = log10(n_H / u_n)
             f6 = log10(dt Gamma_HI + 1e-30)   (ionisations per atom in one step)
             f7 = log10(1 + 4 pi eta dt / E)   (local source over field)
             f8 = log10(dt / 1e12 s)
-            (species fractions floored at 1e-30; H-only runs set f3 = f4 = 0)
+            f9 = log10(E / E^{n-1})    f10 = log10(e / e^{n-1})
+            f11 = logit x_HI - logit x_HI^{n-1}   (the previous step's change)
+            f12 = log10(dt / dt^{n-1})            (this step over the previous one)
+            (species fractions floored at 1e-30, x_HI in [1e-30, 1 - 1e-16] for the logits;
+            H-only runs set f3 = f4 = 0; without a previous step f9..f12 = 0)
   outputs   o0 = log10(E' / E)   o1 = log10(e' / e)   o2 = logit(n_HI' / n_H)
             o3..o5 = logits of the He fractions (HeI, HeII, HeIII) under a softmax
-  network   9 -> 64 -> 64 -> 64 -> 6, SiLU after the three hidden layers, inputs normalised
+  network   13 -> 64 -> 64 -> 64 -> 6, SiLU after the three hidden layers, inputs normalised
             as (f - mean) / scale.
 
-Weight vector layout (shared with the library's C ABI): W1 (64x9, row major), b1 (64),
-W2 (64x64), b2, W3 (64x64), b3, W4 (6x64), b4 (6), mean (9), scale (9).
+Weight vector layout (shared with the library's C ABI): W1 (64x13, row major), b1 (64),
+W2 (64x64), b2, W3 (64x64), b3, W4 (6x64), b4 (6), mean (13), scale (13).
 """
 import numpy as np
 
 from . import closure as cl
 
-NIN, NHID, NOUT = 9, 64, 6
+NIN, NHID, NOUT = 13, 64, 6
 SHAPES = [("W1", (NHID, NIN)), ("b1", (NHID,)), ("W2", (NHID, NHID)), ("b2", (NHID,)),
           ("W3", (NHID, NHID)), ("b3", (NHID,)), ("W4", (NOUT, NHID)), ("b4", (NOUT,)),
           ("mean", (NIN,)), ("scale", (NIN,))]
@@ -69,8 +74,15 @@ def dsilu(z):
     return s * (1.0 + z * (1.0 - s))
 
 
-def features(p, state, dt, a=1.0):
-    """The 9 input features of every cell of ``p`` (oracle Problem) at the given state."""
+def _logit_hi(n, nH):
+    x = np.clip(n / nH, FLOOR, 1.0 - 1e-16)
+    return np.log(x) - np.log1p(-x)
+
+
+def features(p, state, dt, a=1.0, prev=None, dt_prev=None):
+    """The 13 input features of every cell of ``p`` (oracle Problem) at the given state, with
+    the previous step's state ``prev`` (E, e, n) and length ``dt_prev`` (None: no previous
+    step)."""
     E = np.asarray(state["E"]).ravel()
     e = np.asarray(state["e"]).ravel()
     n = np.asarray(state["n"]).reshape(p.ns, -1)
@@ -91,6 +103,15 @@ def features(p, state, dt, a=1.0):
     X[:, 6] = np.log10(dt * gam + FLOOR)
     X[:, 7] = np.log10(1.0 + p.src * dt / E)
     X[:, 8] = np.log10(dt / 1e12)
+    X[:, 9:13] = 0.0
+    if prev is not None:
+        E0 = np.asarray(prev["E"]).ravel()
+        e0 = np.asarray(prev["e"]).ravel()
+        n0 = np.asarray(prev["n"]).reshape(p.ns, -1)
+        X[:, 9] = np.log10(E / E0)
+        X[:, 10] = np.log10(e / e0)
+        X[:, 11] = _logit_hi(n[0], nH) - _logit_hi(n0[0], nH)
+        X[:, 12] = np.log10(dt / dt_prev)
     return X
 
 

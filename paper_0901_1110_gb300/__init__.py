@@ -137,7 +137,7 @@ def rhi_grey_constants(spectrum, param, n_species):
 
 
 RHI_NOALLOC_MAX_COUNT = 33554432
-RHI_MLP_IN, RHI_MLP_HID, RHI_MLP_OUT = 9, 64, 6
+RHI_MLP_IN, RHI_MLP_HID, RHI_MLP_OUT = 13, 64, 6
 RHI_MLP_NWEIGHTS = (RHI_MLP_HID * RHI_MLP_IN + RHI_MLP_HID + 2 * (RHI_MLP_HID * RHI_MLP_HID + RHI_MLP_HID)
                     + RHI_MLP_OUT * RHI_MLP_HID + RHI_MLP_OUT + 2 * RHI_MLP_IN)
 
@@ -305,7 +305,7 @@ class Solver:
         return w
 
     def mlp_features(self, dt, a=1.0, out=None):
-        """Features (N x 9, float32) of the current state; into `out` (array or tensor) if given."""
+        """Features (N x 13, float32) of the current state; into `out` (array or tensor) if given."""
         X = np.empty((self.N, RHI_MLP_IN), dtype=np.float32) if out is None else out
         pX, dev = _fptr(X, self.N * RHI_MLP_IN)
         self._check(lib().rhi_mlp_features(self.h, dt, a, pX, dev), "rhi_mlp_features")
@@ -355,7 +355,7 @@ class Solver:
         return loss.value, g
 
     def mlp_train(self, X, Y, epochs=1, batch=4096, lr=1e-3):
-        """Adam over device tensors X (n x 9), Y (n x 6); returns the last epoch's mean loss."""
+        """Adam over device tensors X (n x 13), Y (n x 6); returns the last epoch's mean loss."""
         n = X.shape[0]
         (pX, d0), (pY, d1) = _fptr(X, n * RHI_MLP_IN), _fptr(Y, n * RHI_MLP_OUT)
         if not (d0 and d1):

@@ -105,6 +105,11 @@ struct rhi_ctx {
     // state U^n
     double *E_s = nullptr, *e_s = nullptr, *n_s = nullptr, *nH = nullptr, *src = nullptr,
            *Tiso = nullptr;
+    // the state before the last accepted step and that step's length (the learned guess's
+    // view of the previous change; ionization model only)
+    double *E_p = nullptr, *e_p = nullptr, *n_p = nullptr;
+    double dt_prev = 0.0;
+    bool have_prev = false;
     // two work iterates, contiguous (e_c | n_1 .. | E), their opacity and face coefficients
     double* U[2] = {nullptr, nullptr};
     double* kap[2] = {nullptr, nullptr};
@@ -934,6 +939,10 @@ MlpArgs mlp_args(const rhi_ctx* h, double dt, double a) {
     A.gate = (float)h->prm.mlp_gate;
     A.ood = (float)h->prm.mlp_ood;
     A.isothermal = h->prm.isothermal;
+    if (h->have_prev) {
+        A.E_p = h->E_p; A.e_p = h->e_p; A.n_p = h->n_p;
+        A.ldt_ratio = (float)std::log10(dt / h->dt_prev);
+    }
     return A;
 }
 
@@ -1051,6 +1060,7 @@ int rhi_create(const rhi_grid* grid, const rhi_bc* bc, const rhi_params* params,
     auto A = [&](double** p, size_t n) { if (!rc) rc = dalloc(h, p, n); };
     A(&h->E_s, N); A(&h->e_s, N); A(&h->n_s, (size_t)h->ns * N); A(&h->nH, N); A(&h->src, N);
     A(&h->Tiso, N);
+    if (h->ns > 0) { A(&h->E_p, N); A(&h->e_p, N); A(&h->n_p, (size_t)h->ns * N); }
     for (int b = 0; b < 2; ++b) {
         A(&h->U[b], (size_t)h->nv * N); A(&h->kap[b], N); A(&h->W[b], 3 * (size_t)N);
         A(&h->diag[b], N); A(&h->rhs[b], N); A(&h->fMt[b], (size_t)h->nm * N);
@@ -1592,7 +1602,15 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
         S.eps_loc = pn < 0.0 ? v : std::pow(v / ((double)N * h->nv), 1.0 / pn);
         S.dt_next = S.eps_loc > 0.0 ? h->prm.dt_tau_tol * dt / S.eps_loc : HUGE_VAL;
     }
-    // ---- accept: U^{n+1} -> state, e^{n+1} = e_h + e_c
+    // ---- accept: U^n -> the previous state (the learned guess's features), U^{n+1} -> state,
+    // e^{n+1} = e_h + e_c
+    if (h->E_p) {
+        CK(cudaMemcpyAsync(h->E_p, h->E_s, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        CK(cudaMemcpyAsync(h->e_p, h->e_s, N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        CK(cudaMemcpyAsync(h->n_p, h->n_s, (size_t)ns * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+        h->have_prev = true;
+        h->dt_prev = dt;
+    }
     if (cur >= 0) {
         {
             Scope s(h->prof, "finalize_energy");

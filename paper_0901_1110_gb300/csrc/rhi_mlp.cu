@@ -1,9 +1,12 @@
 // Learned Newton initial guess (an addition to the paper's method, whose Sec. 3.2 leaves the
 // initial iterate free and whose Sec. 3.2.4 uses an explicit predictor): a per-cell MLP
-// 9 -> 64 -> 64 -> 64 -> 6 with SiLU that predicts the state at t^{n+1} from the state at t^n.
+// 13 -> 64 -> 64 -> 64 -> 6 with SiLU that predicts the state at t^{n+1} from the state at
+// t^n and the change of the previous step.
 //
 //   features  log10 E/u_E, log10 e/u_e, log10 x_HI, log10 x_HeI, log10 x_HeII, log10 n_H/u_n,
-//             log10(dt Gamma_HI + 1e-30), log10(1 + 4 pi eta dt / E), log10(dt / 1e12 s)
+//             log10(dt Gamma_HI + 1e-30), log10(1 + 4 pi eta dt / E), log10(dt / 1e12 s),
+//             log10 E/E^{n-1}, log10 e/e^{n-1}, logit x_HI - logit x_HI^{n-1},
+//             log10(dt / dt^{n-1}) (the last four 0 before a first step)
 //   outputs   log10 E'/E, log10 e'/e, logit x_HI', He fraction logits (softmax)
 //
 // Inference runs on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation)
@@ -48,6 +51,18 @@ __device__ __forceinline__ void cell_features(const MlpArgs& A, long long c, flo
     f[6] = log10_clamped(A.dt * A.gam_per_E * E + 1e-30);
     f[7] = log10f(1.0f + fminf((float)(A.src[c] * A.dt / E), 1e37f));
     f[8] = log10_clamped(A.dt * 1e-12);
+    if (A.E_p) {
+        // the previous step's change: ratios in FP64, the logit difference in FP64 (neutral
+        // cells sit within 1e-16 of x_HI = 1), rounded to FP32
+        f[9] = log10_clamped(E / A.E_p[c]);
+        f[10] = log10_clamped(e / A.e_p[c]);
+        const double x1 = fmin(fmax(A.n[c] * inH, 1e-30), 1.0 - 1e-16);
+        const double x0 = fmin(fmax(A.n_p[c] * inH, 1e-30), 1.0 - 1e-16);
+        f[11] = (float)((log(x1) - log1p(-x1)) - (log(x0) - log1p(-x0)));
+        f[12] = A.ldt_ratio;
+    } else {
+        f[9] = f[10] = f[11] = f[12] = 0.0f;
+    }
 }
 
 __global__ void k_mlp_features(const MlpArgs A, float* __restrict__ X) {

@@ -35,6 +35,11 @@ struct MlpArgs {
     const double* n;
     const double* nH;
     const double* src;
+    // the state before the last accepted step (null: none yet) and log10(dt / dt^{n-1})
+    const double* E_p;
+    const double* e_p;
+    const double* n_p;
+    float ldt_ratio;
     float gate;
     float ood;                                // |normalised feature| above this keeps U^n
     int isothermal;                           // guess keeps e_c = 0

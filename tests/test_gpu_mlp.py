@@ -87,8 +87,14 @@ def test_features_and_targets_match_oracle(rhi):
     s.step(w.dt, newton_tol=1e-10, lin_tol=1e-10)
     Y = s.mlp_targets(old)
     new = s.get_state()
-    Yr = om.targets(p, dict(E=old["E"], e=old["e"], n=old["n"].reshape(w.ns, -1)), new)
+    old_n = dict(E=old["E"], e=old["e"], n=old["n"].reshape(w.ns, -1))
+    Yr = om.targets(p, old_n, new)
     np.testing.assert_allclose(Y, Yr, rtol=2e-6, atol=2e-5)
+    # after a step the features carry its change, here for a next step of half the length
+    X = s.mlp_features(0.5 * w.dt, a=0.7)
+    Xr = om.features(p, new, 0.5 * w.dt, a=0.7, prev=old_n, dt_prev=w.dt)
+    assert np.abs(Xr[:, 9:12]).max() > 1e-3
+    np.testing.assert_allclose(X, Xr, rtol=2e-6, atol=2e-5)
 
 
 def test_tensor_core_forward_matches_oracle(rhi):
@@ -97,13 +103,13 @@ def test_tensor_core_forward_matches_oracle(rhi):
     error stays at the percent level of the output scale; ragged row counts and the
     64-row tiles both covered."""
     rng = np.random.default_rng(0)
-    w = _normalised(om.init_weights(7), rng.standard_normal((256, 9)) * 3 + 1)
+    w = _normalised(om.init_weights(7), rng.standard_normal((256, om.NIN)) * 3 + 1)
     s = rhi.Solver(2, 2, 2, 1.0, rhi.rhi_params_default(1))
     s.mlp_set_weights(w.astype(np.float32))
     w32 = s.mlp_get_weights()
     assert np.array_equal(w32, w.astype(np.float32))
     for n in (1, 31, 33, 1000, 4099):
-        X = (rng.standard_normal((n, 9)) * 3 + 1).astype(np.float32)
+        X = (rng.standard_normal((n, om.NIN)) * 3 + 1).astype(np.float32)
         Y = s.mlp_forward(X)
         Yr = om.forward(w32.astype(np.float64), X.astype(np.float64))
         scale = max(1.0, float(np.abs(Yr).max()))
@@ -117,18 +123,18 @@ def test_gradient_matches_oracle(rhi):
     """FP32 per-sample backward + deterministic weight-gradient reduction vs the FP64 oracle
     gradient (normwise 1e-4) and loss (1e-5), with a ragged sample count."""
     rng = np.random.default_rng(1)
-    w = _normalised(om.init_weights(2), rng.standard_normal((64, 9)))
+    w = _normalised(om.init_weights(2), rng.standard_normal((64, om.NIN)))
     w32 = w.astype(np.float32)
     s = rhi.Solver(2, 2, 2, 1.0, rhi.rhi_params_default(1))
     s.mlp_set_weights(w32)
     for n in (1, 200, 3001):
-        X = rng.standard_normal((n, 9)).astype(np.float32)
+        X = rng.standard_normal((n, om.NIN)).astype(np.float32)
         Y = rng.standard_normal((n, 6)).astype(np.float32)
         loss, g = s.mlp_loss_grad(X, Y)
         lr, gr = om.loss_and_grad(w32.astype(np.float64), X.astype(np.float64), Y.astype(np.float64))
         assert abs(loss / lr - 1) < 1e-5
         assert np.linalg.norm(g - gr) <= 1e-4 * np.linalg.norm(gr), n
-        assert np.all(g[-18:] == 0)
+        assert np.all(g[-2 * om.NIN:] == 0)
     s.close()
 
 

@@ -61,6 +61,16 @@ def test_features_of_a_known_cell():
     np.testing.assert_allclose(X[:, 2], np.log10(0.75), rtol=1e-15)
     np.testing.assert_allclose(X[:, 5], 0.0, atol=1e-15)
     np.testing.assert_allclose(X[:, 8], 0.0, atol=1e-15)
+    np.testing.assert_array_equal(X[:, 9:13], 0.0)                   # no previous step
+    # a previous step with half the field, a quarter more gas energy, x_HI from 0.5 to 0.75,
+    # and twice the step length
+    st = w.state()
+    prev = dict(E=st["E"] * 0.5, e=st["e"] * 1.25, n=st["n"] * (0.5 / 0.75))
+    X = mlp.features(p, st, 1e12, prev=prev, dt_prev=2e12)
+    np.testing.assert_allclose(X[:, 9], np.log10(2.0), rtol=1e-15)
+    np.testing.assert_allclose(X[:, 10], -np.log10(1.25), rtol=1e-14)
+    np.testing.assert_allclose(X[:, 11], np.log(3.0), rtol=1e-14)       # logit 3/4 - logit 1/2
+    np.testing.assert_allclose(X[:, 12], -np.log10(2.0), rtol=1e-15)
 
 
 def test_out_of_distribution_cells_keep_the_old_state():
