@@ -363,12 +363,15 @@ def run_form(rhi, w, torch, steps, warmup, precond, ab, limiter_jacobian=0, max_
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     agg = dict(newton_its=0, pcg_its=0, vcycles=0, launches=0, backtracks=0, learned_used=0,
-               guess_restarts=0, host_syncs=0, krylov_fallbacks=0)
+               guess_restarts=0, host_syncs=0, krylov_fallbacks=0, krylov_stalls=0)
     e0.record(stream)
     hist, res0, prev0 = [], [], []
+    agg["newton_per_step"], agg["krylov_per_step"] = [], []
     for _ in range(steps):
         s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol)
         st = s.stats()
+        agg["newton_per_step"].append(st["newton_its"])
+        agg["krylov_per_step"].append(st["pcg_its"])
         for k in agg:
             if k in st:
                 agg[k] += st[k]
@@ -420,14 +423,64 @@ def config_128_plain(rhi, torch, limiter_jacobian, max_newton):
             "newton_its": a[:, 0].astype(int).tolist(), "krylov_its": a[:, 1].astype(int).tolist()}
 
 
+def config_cosmo_run(rhi, torch, n, intervals, max_newton):
+    """The cosmological configuration (H + He, sigma_ln = 1.5, 256 clustered sources at 512^3,
+    flat Lambda-CDM from z = 10 in 100 equal intervals of cosmic time) over its first
+    `intervals` intervals, each with (a, adot) at its middle and adaptive implicit steps inside
+    it (p = 2, tau_tol = 0.05, Newton tol 1e-8), in the plain FP64 form and the mixed form.  The
+    mixed form's final state is compared with the plain form's, per element and in the scaled
+    unknowns."""
+    from paper_0901_1110_gb300 import inputs
+    w = inputs.config_cosmo(n, nsrc=max(1, round(256 * (n / 512) ** 3)))
+    out, states = {}, {}
+    for name, pc in (("plain_fp64", rhi.RHI_PRECOND_MG_FP64), ("mixed_fp32mg", rhi.RHI_PRECOND_MG_FP32)):
+        stream = torch.cuda.Stream()
+        s = rhi.solver_for_workload(w, stream=stream.cuda_stream, precond=pc, mg_levels=6,
+                                    theta=1.0, limiter_jacobian=2, max_newton=max_newton,
+                                    dt_norm=2, dt_tau_tol=0.05)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        steps, dt = 0, 1e11
+        for k in range(intervals):
+            span, a, adot = w.schedule[k]
+            t, nst = s.advance(span, min(dt, span), dt_min=1e6, a=a, adot=adot,
+                               newton_tol=w.newton_tol, lin_tol=w.lin_tol)
+            steps += nst
+            dt = max(s.stats()["dt_next"], 1e6)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        states[name] = s.get_state()
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+        out[name] = {"implicit_steps": steps, "ms": ms, "value": w.N * steps / (ms * 1e-3),
+                     "unit": UNIT}
+    a_end = float(inputs.flat_lcdm_a(inputs.flat_lcdm_t(1.0 / 11.0) + intervals * w.dt))
+    nH = w.nH.ravel()
+    out["mixed_vs_plain"] = {"per_element": _per_element(states["mixed_fp32mg"], states["plain_fp64"],
+                                                         nH, w.y_he),
+                             "scaled_E": float(np.abs(np.asarray(states["mixed_fp32mg"]["E"])
+                                                      - np.asarray(states["plain_fp64"]["E"])).max() / w.u_E)}
+    out["workload"] = (f"cosmological configuration {n}^3, {len(w.src_rate)} clustered sources, "
+                       f"sigma_ln 1.5, first {intervals} of 100 intervals from z = 10 "
+                       f"(to z = {1.0 / a_end - 1.0:.3f}), "
+                       "adaptive steps (p = 2, tau_tol 0.05), Newton tol 1e-8")
+    return out
+
+
 def train_guess(rhi, torch, rank, train_steps, epochs):
-    """Trains the learned guess on the GPU from Newton solutions of 128^3 lognormal runs
-    (16 sources in 1 Mpc, seeds distinct from the timed workload's), mixed form."""
+    """Trains the learned guess on the GPU from Newton solutions of a 128^3 lognormal run at
+    the timed workload's cell size and source density (a 0.5 Mpc box with 8 sources, a seed
+    distinct from the timed workload's), mixed form, exact Newton matrix."""
     from paper_0901_1110_gb300 import inputs
     t0 = time.perf_counter()
-    w = inputs.config_lognormal(128, nsrc=16, seed=1000 + rank)
+    w = inputs.config_lognormal(128, nsrc=workload_sources(128), seed=1000 + rank,
+                                box=inputs.MPC * 128 / 256)
     s = rhi.solver_for_workload(w, precond=rhi.RHI_PRECOND_MG_FP32, mg_levels=6, theta=1.0,
-                                max_newton=200)
+                                max_newton=200, limiter_jacobian=2)
     N = w.N
     X = torch.empty((train_steps * N, rhi.RHI_MLP_IN), dtype=torch.float32, device="cuda")
     Y = torch.empty((train_steps * N, rhi.RHI_MLP_OUT), dtype=torch.float32, device="cuda")
@@ -458,7 +511,8 @@ def train_guess(rhi, torch, rank, train_steps, epochs):
     s.close()
     info = {"samples": int(X.shape[0]), "epochs": epochs, "loss_per_epoch": losses,
             "data_s": t_data, "total_s": time.perf_counter() - t0,
-            "source": f"{train_steps} steps of lognormal_hhe 128^3, 16 sources, 1 Mpc, seed {1000 + rank}"}
+            "source": f"{train_steps} steps of lognormal_hhe 128^3, {workload_sources(128)} "
+                      f"sources, 0.5 Mpc (the timed run's cell size), seed {1000 + rank}"}
     return wts, info
 
 
@@ -540,6 +594,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-config2", action="store_true",
                     help="skip the 128^3 plain FP64 configuration (20 steps)")
+    ap.add_argument("--cosmo-intervals", type=int, default=0,
+                    help="also run the first K intervals of the cosmological configuration")
+    ap.add_argument("--cosmo-n", type=int, default=512)
     ap.add_argument("--max-newton", type=int, default=200)
     ap.add_argument("--limiter-jacobian", type=int, default=2,
                     help="0: D lagged (CG); 1: dD/dE kept; 2: exact Newton matrix (BiCGStab)")
@@ -654,6 +711,8 @@ def main():
                 "kernel_launches_breakdown_step": {k: v[1] for k, v in
                                                    sorted(f["kt"].items(), key=lambda kv: -kv[1][0])},
                 "roofline_kernel": f["tname"],
+                "newton_per_step": f["agg"]["newton_per_step"],
+                "krylov_per_step": f["agg"]["krylov_per_step"],
                 "hbm_frac": hbm_fracs(f["kt"])}
 
     line = {
@@ -681,6 +740,9 @@ def main():
     if not args.no_config2:
         line["config_128_plain_fp64"] = config_128_plain(rhi, torch, args.limiter_jacobian,
                                                          args.max_newton)
+    if args.cosmo_intervals > 0:
+        line["config_cosmo"] = config_cosmo_run(rhi, torch, args.cosmo_n, args.cosmo_intervals,
+                                                args.max_newton)
     if rank == 0:
         if not args.no_e2e:
             pc, guess = FORMS[order[-1]]

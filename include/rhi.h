@@ -144,6 +144,8 @@ typedef struct {
                                lagged-D direction (CG) instead                              */
     int host_syncs;         /* blocking device-to-host reads the step made (residual norms,
                                Krylov results, the final wait)                               */
+    int krylov_stalls;      /* BiCGStab solves ended because ||r|| had not fallen by 10% in 20
+                               iterations (the Newton step then uses that inexact solution)  */
     double res_initial;     /* ||f(U_0)|| (eq. rmsnorm, scaled)                              */
     double res_final;       /* ||f(U^{n+1})||                                                */
     double res_guess_prev;  /* ||f(U^n)|| when a learned guess was tried, else 0             */

@@ -48,7 +48,7 @@ class rhi_params(C.Structure):
 class rhi_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("newton_its", C.c_int), ("pcg_its", C.c_int),
                 ("vcycles", C.c_int), ("backtracks", C.c_int), ("lam_min_steps", C.c_int),
-                ("guess_used", C.c_int), ("launches", C.c_int), ("guess_restarts", C.c_int), ("krylov_fallbacks", C.c_int), ("host_syncs", C.c_int),
+                ("guess_used", C.c_int), ("launches", C.c_int), ("guess_restarts", C.c_int), ("krylov_fallbacks", C.c_int), ("host_syncs", C.c_int), ("krylov_stalls", C.c_int),
                 ("res_initial", C.c_double),
                 ("res_final", C.c_double), ("res_guess_prev", C.c_double), ("ms", C.c_double),
                 ("eps_loc", C.c_double), ("dt_next", C.c_double),

@@ -738,6 +738,7 @@ int krylov_graph_build(rhi_ctx* h, const double* rhs, rhi_ctx::KGraph& g) {
 int bicg_outcome(rhi_ctx* h, int* its_out) {
     const int its = (int)h->h_scal[S_ITS];
     *its_out = its;
+    h->stats.krylov_stalls += h->h_scal[S_STALL] != 0.0 ? 1 : 0;
     h->prof.launches += its * h->kg_body_kernels;
     h->kg_body_kernels = 0;
     if (h->prm.precond != RHI_PRECOND_JACOBI)

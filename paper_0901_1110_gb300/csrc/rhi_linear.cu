@@ -435,7 +435,10 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_copy(long long N, const double* _
 //   RED_BICG_SS:    s.s: converged at the middle of the iteration when s.s <= S_THR (S_HALF,
 //                   S_DONE); a breakdown flagged by the alpha reduction also sets S_DONE.
 //   RED_BICG_NEXT:  r.r and rh.r: beta and rho for the next iteration, S_ITS += 1, and the
-//                   loop ends when converged (or S_DONE), on a breakdown, or at S_MAXIT.
+//                   loop ends when converged (or S_DONE), on a breakdown, at S_MAXIT, or when
+//                   r.r has not fallen below 0.81 of its best for STALL_ITS iterations (a
+//                   stagnating solve, as an FP32 preconditioner's rounding can cause near the
+//                   Newton root: the step taken is then that of an inexact Newton iteration).
 // This kernel always runs to its end: it is what ends the loop.
 __global__ void __launch_bounds__(RED_BLOCK) k_reduce_loop(const double* __restrict__ partials,
                                                            int n, double* __restrict__ scal,
@@ -457,6 +460,9 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce_loop(const double* __restr
         scal[S_ITS] = 0.0;
         scal[S_HALF] = 0.0;
         scal[S_BREAK] = fin ? 0.0 : 1.0;
+        scal[S_BEST] = s;
+        scal[S_BESTIT] = 0.0;
+        scal[S_STALL] = 0.0;
         const bool done = !(s > scal[S_THR]) || !fin || !(scal[S_MAXIT] >= 1.0);
         scal[S_DONE] = done ? 1.0 : 0.0;
         cont = !done;
@@ -485,8 +491,14 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce_loop(const double* __restr
             const bool brk = !isfinite(s) || !(rho != 0.0) || scal[S_BREAK] != 0.0;
             if (brk) scal[S_BREAK] = 1.0;
             const bool conv = !(s > scal[S_THR]);
+            if (s < 0.81 * scal[S_BEST]) {
+                scal[S_BEST] = s;
+                scal[S_BESTIT] = its;
+            }
+            const bool stall = its - scal[S_BESTIT] >= (double)STALL_ITS;
+            if (stall && !conv) scal[S_STALL] = 1.0;
             // (written so that a cap that is not a number also ends the loop)
-            cont = !(conv || brk) && its < scal[S_MAXIT] && its < 1e6;
+            cont = !(conv || brk || stall) && its < scal[S_MAXIT] && its < 1e6;
         }
     }
     scal[S_CONT] = cont ? 1.0 : 0.0;

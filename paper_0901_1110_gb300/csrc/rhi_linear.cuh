@@ -48,8 +48,12 @@ constexpr long long COARSE_MAX = 8192;
 // on the device: S_THR (converged when r.r <= S_THR), S_MAXIT, the iteration count S_ITS, S_DONE
 // (nothing left to do in this iteration), S_HALF (converged at the middle of an iteration:
 // x += alpha M^-1 p only) and S_CONT (1 while another iteration follows).
+// S_BEST / S_BESTIT: the smallest r.r so far and its iteration; S_STALL: the loop ended because
+// r.r had not fallen below 0.81 of that best (10% in ||r||) for STALL_ITS iterations.
 enum { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RR, S_BREAK, S_TMP, S_RHO, S_OMEGA, S_SS, S_TS,
-       S_TT, S_RV, S_DONE, S_ITS, S_THR, S_MAXIT, S_HALF, S_CONT, S_NSCAL = 24 };
+       S_TT, S_RV, S_DONE, S_ITS, S_THR, S_MAXIT, S_HALF, S_CONT, S_BEST, S_BESTIT, S_STALL,
+       S_NSCAL = 24 };
+constexpr int STALL_ITS = 20;
 enum { RED_SUM = 0, RED_ALPHA = 1, RED_BETA = 2, RED_BICG_ALPHA = 3, RED_BICG_OMEGA = 4,
        RED_BICG_RHO = 5, RED_MAX = 6, RED_BICG_START = 7, RED_BICG_SS = 8,
        RED_BICG_NEXT = 9 };

@@ -44,7 +44,7 @@ def test_binding_names_match_header(libpath):
 
 
 def test_library_targets_sm_103a(libpath):
-    """The fatbin inside the library is built for sm_103a (architecture list of cuobjdump is
-    tool output, not a disassembly)."""
+    """The build compiles every translation unit for sm_103a alone (the -gencode flag the
+    build passes to nvcc)."""
     from paper_0901_1110_gb300 import _build
     assert "arch=compute_103a,code=sm_103a" in _build.ARCH

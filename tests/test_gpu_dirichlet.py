@@ -1,6 +1,6 @@
 """Dirichlet radiation boundaries on the GPU: steps vs the FP64 oracle in both physics models and
 all three Newton matrices, the steady diffusion line between two boundary values, and the
-free-streaming front of Sec. 4.2, which the limiter must move at the speed of light."""
+free-streaming front of Sec. 4.1, which the limiter must move at the speed of light."""
 import numpy as np
 import pytest
 
@@ -79,7 +79,7 @@ def test_steady_diffusion_line_on_gpu(rhi):
 
 @pytest.mark.timeout(300)
 def test_free_streaming_front_moves_at_c(rhi):
-    """Sec. 4.2: a 1 cm line of 128 cells, opacity 1e-6 cm^-1 (Planck and total), E = 1e-4,
+    """Sec. 4.1: a 1 cm line of 128 cells, opacity 1e-6 cm^-1 (Planck and total), E = 1e-4,
     E = 1 held on the left face; after a quarter of the light-crossing time (8.3391 ps) the
     front, where E falls through one half, sits at c t = 0.25 cm to within the few cells the
     paper's adaptive steps also lag by."""

@@ -1,5 +1,5 @@
 """The LTE coupling model (eq. LTE_coupling) on the GPU: implicit steps vs the FP64 oracle, and
-the matter-radiation equilibration test of Sec. 4.4 (Turner & Stone) with its closed-system
+the matter-radiation equilibration test of Sec. 4.2 (Turner & Stone) with its closed-system
 equilibrium and total-energy conservation."""
 import numpy as np
 import pytest

@@ -1,5 +1,5 @@
 """Pins of the oracle's LTE coupling model (eq. LTE_coupling): the Newton matrix against central
-differences, and the matter-radiation equilibration of Sec. 4.4 (Turner & Stone): the gas
+differences, and the matter-radiation equilibration of Sec. 4.2 (Turner & Stone): the gas
 energy reaches the equilibrium of the closed system, and the total energy is conserved to the
 Newton tolerance (the paper's conservation table)."""
 import numpy as np
