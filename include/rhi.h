@@ -115,6 +115,11 @@ typedef struct {
                                non-symmetric 7-point matrix, whose coarse levels then carry
                                both couplings of each face); 0 the lagged-D matrix
                                (symmetric), as a preconditioner of the Newton matrix        */
+    double krylov_restart;  /* BiCGStab restarts (shadow residual set to the current residual)
+                               each time ||r|| has fallen below this fraction of its value at
+                               the last start; 0: only on stagnation (||r|| not 10% below its
+                               best for 20 iterations); at most 8 restarts per solve.
+                               Negative (default): 0.01 with the FP32 multigrid, else 0      */
     int dt_norm;            /* adaptive time steps (Sec. 3.2.3): 0 off; p >= 1 the p-norm and
                                -1 the max norm of eq. time_error_estimator                  */
     double dt_tau_tol;      /* tau_tol of eq. time_step_selection                            */
@@ -161,7 +166,7 @@ typedef struct rhi_ctx* rhi_handle;
    (limiter_jacobian 0), tau 0.99, lam_min 1/16, growth_max 1e3, watchdog 3, max_newton 50,
    max_pcg 200, previous-step guess, FP64 multigrid with 6 levels, 2 + 2 sweeps, 16 coarse
    sweeps, omega 0.9, V-cycle graph on, BiCGStab graph on, multigrid of the Newton matrix
-   (mg_matrix 1),
+   (mg_matrix 1), krylov_restart -1 (0.01 with the FP32 multigrid, else 0),
    learned-guess gates mlp_gate 1e-3, mlp_ood 6,
    mlp_restart 12, mlp_retry 4, fixed steps (dt_norm 0) with tau_tol 0.01, scalings 1,
    kappa_floor 1e-40, mu 0.6, and the grey constants of 13.6 eV monochromatic radiation with a

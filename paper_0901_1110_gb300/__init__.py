@@ -38,7 +38,7 @@ class rhi_params(C.Structure):
                 ("max_newton", C.c_int), ("max_pcg", C.c_int), ("guess", C.c_int),
                 ("precond", C.c_int), ("mg_levels", C.c_int), ("mg_pre", C.c_int),
                 ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double), ("vcycle_graph", C.c_int),
-                ("krylov_graph", C.c_int), ("mg_matrix", C.c_int),
+                ("krylov_graph", C.c_int), ("mg_matrix", C.c_int), ("krylov_restart", C.c_double),
                 ("dt_norm", C.c_int), ("dt_tau_tol", C.c_double), ("model", C.c_int),
                 ("kappa_total", C.c_double), ("kappa_planck", C.c_double), ("mu", C.c_double),
                 ("sk", C.c_double * 3), ("pgam", C.c_double * 3), ("ph", C.c_double * 3),

@@ -167,7 +167,7 @@ struct rhi_ctx {
     std::vector<KGraph> kg;
     cudaStream_t kst = nullptr;           // capture stream
     bool kg_failed = false;
-    double* h_ctl = nullptr;              // pinned: S_THR, S_MAXIT of the next solve
+    double* h_ctl = nullptr;              // pinned: S_THR, S_MAXIT, S_INNER of the next solve
     int host_syncs = 0;                   // blocking device-to-host reads of the last step
     int kg_body_kernels = 0;              // kernels per iteration of the last graph solve
 
@@ -644,7 +644,7 @@ int bicg_iteration(rhi_ctx* h, LinLaunch& L, unsigned long long cond) {
     const long long N = h->N;
     int np = 0, rc;
     L.skip = nullptr;
-    CK(L.bicg_p(N, h->scal, h->r, h->v, h->p, -1));
+    CK(L.bicg_p(N, h->scal, h->r, h->v, h->p, -1, h->rh));
     if ((rc = precond_into(h, L, h->p, h->ph))) return rc;
     CK(L.matvec_ns(h->opns, h->ph, h->v, h->rh, 0, h->partials, np));
     CK(L.reduce(h->partials, np, h->scal, RED_BICG_ALPHA, 0));
@@ -759,7 +759,13 @@ int bicgstab(rhi_ctx* h, const double* rhs, double tol, int* its_out, bool defer
     const long long N = h->N;
     h->h_ctl[0] = tol * tol * (double)N * h->nv;                   // S_THR: bound on r.r
     h->h_ctl[1] = (double)h->prm.max_pcg;                           // S_MAXIT
-    CK(cudaMemcpyAsync(h->scal + S_THR, h->h_ctl, 2 * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    // S_INNER: a restart each time ||r|| falls below krylov_restart of its value at the start.
+    // With the FP32 preconditioner, whose rounding slowly erodes the bi-orthogonality, every
+    // hundredfold reduction by default; with FP64 only on stagnation.
+    double kr = h->prm.krylov_restart;
+    if (kr < 0.0) kr = h->prm.precond == RHI_PRECOND_MG_FP32 ? 1e-2 : 0.0;
+    h->h_ctl[2] = kr * kr;
+    CK(cudaMemcpyAsync(h->scal + S_THR, h->h_ctl, 3 * sizeof(double), cudaMemcpyHostToDevice, h->st));
     int rc = RHI_OK;
     if (krylov_graph_usable(h)) {
         const void* key[6] = {rhs, h->opns.diag, h->opns.P[0], h->pc0.diag, h->pc0.W[0],
@@ -899,6 +905,7 @@ int validate_params(const rhi_params* p) {
     if (p->mg_levels < 1 || p->mg_pre < 1 || p->mg_post < 0 || p->mg_coarse_sweeps < 1) return 0;
     if (p->limiter_jacobian < 0 || p->limiter_jacobian > 2) return 0;
     if (p->mg_matrix != 0 && p->mg_matrix != 1) return 0;
+    if (!(p->krylov_restart < 1.0)) return 0;
     if (p->krylov_graph != 0 && p->krylov_graph != 1) return 0;
     if (!(p->mg_omega > 0.0 && p->mg_omega <= 1.0)) return 0;
     if (p->vcycle_graph != 0 && p->vcycle_graph != 1) return 0;
@@ -1015,6 +1022,7 @@ int rhi_params_default(rhi_params* p, int n_species) {
     p->mg_omega = 0.9;
     p->vcycle_graph = 1;
     p->mg_matrix = 1;
+    p->krylov_restart = -1.0;
     p->krylov_graph = 1;
     p->dt_norm = 0;
     p->dt_tau_tol = 0.01;
@@ -1084,7 +1092,7 @@ int rhi_create(const rhi_grid* grid, const rhi_bc* bc, const rhi_params* params,
     if (!rc) rc = mg_build_levels(h);
     if (!rc) {
         cudaError_t e = cudaMallocHost(&h->h_scal, sizeof(double) * S_NSCAL);
-        if (e == cudaSuccess) e = cudaMallocHost(&h->h_ctl, sizeof(double) * 2);
+        if (e == cudaSuccess) e = cudaMallocHost(&h->h_ctl, sizeof(double) * 3);
         if (e != cudaSuccess) rc = fail(h, RHI_ERR_CUDA, "cudaMallocHost");
     }
     if (!rc) {

@@ -8,6 +8,8 @@
 // lower cell, Wp the lower cell's row to the upper cell.  Symmetric levels pass Wp = W.
 #include "rhi_linear.cuh"
 
+#include <type_traits>
+
 namespace rhi {
 
 constexpr int LIN_BLOCK = 256;
@@ -226,6 +228,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce(const double* __restrict__
             scal[S_BETA] = s / scal[S_RZ];
             scal[S_RZ] = s;
         } else if (op == RED_BICG_ALPHA) {          // s = rh.v
+            scal[S_RST] = 0.0;                      // a restart's p and rh are in place
             scal[S_RV] = s;
             if (!(s != 0.0)) scal[S_BREAK] = 1.0;
             scal[S_ALPHA] = (s != 0.0) ? scal[S_RHO] / s : 0.0;
@@ -306,16 +309,25 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_bicg_init(long long N, const doub
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-// p = r + beta (p - omega v); first: p = r
+// p = r + beta (p - omega v); first: p = r.  first < 0: decided on the device, p = r at the
+// loop's first iteration and after a restart, when also the shadow vector becomes rh = r
 __global__ void __launch_bounds__(LIN_BLOCK) k_bicg_p(long long N, const double* __restrict__ scal,
                                                       const double* __restrict__ r,
                                                       const double* __restrict__ v,
-                                                      double* __restrict__ p, int first) {
+                                                      double* __restrict__ p, int first,
+                                                      double* __restrict__ rh) {
     const double beta = scal[S_BETA], omega = scal[S_OMEGA];
-    if (first < 0) first = scal[S_ITS] == 0.0;
+    bool restart = false;
+    if (first < 0) {
+        restart = scal[S_RST] != 0.0;
+        first = scal[S_ITS] == 0.0 || restart;
+    }
     for (long long c = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; c < N;
-         c += (long long)gridDim.x * LIN_BLOCK)
-        p[c] = first ? r[c] : r[c] + beta * (p[c] - omega * v[c]);
+         c += (long long)gridDim.x * LIN_BLOCK) {
+        const double rc = r[c];
+        p[c] = first ? rc : rc + beta * (p[c] - omega * v[c]);
+        if (restart && rh) rh[c] = rc;
+    }
 }
 
 // s = r - alpha v; partial s.s
@@ -435,10 +447,13 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_copy(long long N, const double* _
 //   RED_BICG_SS:    s.s: converged at the middle of the iteration when s.s <= S_THR (S_HALF,
 //                   S_DONE); a breakdown flagged by the alpha reduction also sets S_DONE.
 //   RED_BICG_NEXT:  r.r and rh.r: beta and rho for the next iteration, S_ITS += 1, and the
-//                   loop ends when converged (or S_DONE), on a breakdown, at S_MAXIT, or when
-//                   r.r has not fallen below 0.81 of its best for STALL_ITS iterations (a
-//                   stagnating solve, as an FP32 preconditioner's rounding can cause near the
-//                   Newton root: the step taken is then that of an inexact Newton iteration).
+//                   loop ends when converged (or S_DONE), on a breakdown, or at S_MAXIT.
+//                   When r.r has not fallen below 0.81 of its best for STALL_ITS iterations,
+//                   or below S_INNER times its value at the last restart, the next iteration
+//                   restarts with rh = r (up to MAX_RESTARTS times; the rounding of an FP32
+//                   preconditioner slowly erodes the bi-orthogonality BiCGStab relies on); a
+//                   stagnation past the last restart ends the loop, and the Newton step is
+//                   then that of an inexact Newton iteration.
 // This kernel always runs to its end: it is what ends the loop.
 __global__ void __launch_bounds__(RED_BLOCK) k_reduce_loop(const double* __restrict__ partials,
                                                            int n, double* __restrict__ scal,
@@ -463,6 +478,9 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce_loop(const double* __restr
         scal[S_BEST] = s;
         scal[S_BESTIT] = 0.0;
         scal[S_STALL] = 0.0;
+        scal[S_RR0] = s;
+        scal[S_NRST] = 0.0;
+        scal[S_RST] = 0.0;
         const bool done = !(s > scal[S_THR]) || !fin || !(scal[S_MAXIT] >= 1.0);
         scal[S_DONE] = done ? 1.0 : 0.0;
         cont = !done;
@@ -495,7 +513,18 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce_loop(const double* __restr
                 scal[S_BEST] = s;
                 scal[S_BESTIT] = its;
             }
-            const bool stall = its - scal[S_BESTIT] >= (double)STALL_ITS;
+            bool stall = its - scal[S_BESTIT] >= (double)STALL_ITS;
+            const bool inner = scal[S_INNER] > 0.0 && !(s > scal[S_INNER] * scal[S_RR0]);
+            if (!conv && !brk && (stall || inner) && scal[S_NRST] < (double)MAX_RESTARTS) {
+                // restart from the current x and r: fresh shadow vector rh = r, rho = r.r
+                scal[S_RST] = 1.0;
+                scal[S_NRST] += 1.0;
+                scal[S_RR0] = s;
+                scal[S_RHO] = s;
+                scal[S_BEST] = s;
+                scal[S_BESTIT] = its;
+                stall = false;
+            }
             if (stall && !conv) scal[S_STALL] = 1.0;
             // (written so that a cap that is not a number also ends the loop)
             cont = !(conv || brk || stall) && its < scal[S_MAXIT] && its < 1e6;
@@ -530,12 +559,37 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_smooth(const Op<T> A, const T*
     }
 }
 
+// the first sweep of a cycle, from x = 0: x = (omega / diag) b, 16 bytes per thread (N a
+// multiple of 16 / sizeof(T), 16-byte aligned arrays; the launcher checks)
+template <typename T>
+__global__ void __launch_bounds__(LIN_BLOCK) k_mg_smooth_first_vec(long long N,
+                                                                   const T* __restrict__ wid,
+                                                                   const T* __restrict__ b,
+                                                                   T* __restrict__ xout,
+                                                                   const double* skip) {
+    if (skipped(skip)) return;
+    using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    const long long NV = N * (long long)sizeof(T) / 16;
+    for (long long q = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; q < NV;
+         q += (long long)gridDim.x * LIN_BLOCK) {
+        const VT w = __ldg(reinterpret_cast<const VT*>(wid) + q);
+        const VT bb = __ldg(reinterpret_cast<const VT*>(b) + q);
+        VT o;
+        o.x = w.x * bb.x; o.y = w.y * bb.y;
+        if constexpr (sizeof(T) == 4) { o.z = w.z * bb.z; o.w = w.w * bb.w; }
+        reinterpret_cast<VT*>(xout)[q] = o;
+    }
+}
+
 // Weighted-Jacobi sweep marching along z: a thread owns one (i, j) column and ZM consecutive
 // planes, so the x values of the planes above and below and the z-face coefficient shared by
 // two planes stay in registers, and the x / y neighbour offsets are computed once.  The
 // arithmetic is that of k_mg_smooth term for term (the same products summed in the same
-// order), so the result is identical.
-constexpr int ZM = 8;
+// order), so the result is identical.  ZM = 2: every load of both planes is issued before the
+// first use within 56 registers, four blocks per SM; measured at 256^3 (FP32, both couplings
+// per face), 0.91 of the HBM copy bandwidth against 0.61 for ZM = 8 (whose 104 loads do not fit
+// the register budget and were issued in dependent groups) and 0.78 for one cell per thread.
+constexpr int ZM = 2;
 template <typename T>
 __global__ void __launch_bounds__(LIN_BLOCK) k_mg_smooth_zm(const Op<T> A, const T* __restrict__ b,
                                                             const T* __restrict__ xin,
@@ -710,6 +764,36 @@ __global__ void __launch_bounds__(LIN_BLOCK) k_mg_restrict(const Op<T> A, const 
             }
         }
         bc[cc] = acc * T(0.125);
+    }
+}
+
+// x_f += x_c(parent), 16 bytes of fine cells per thread along x (4 FP32 or 2 FP64 cells, whose
+// parents are 2 or 1 consecutive coarse cells); needs nx a multiple of 4 (FP32) or 2 (FP64) and
+// 16-byte aligned rows, which the launcher checks.  fx, fxy divide by nx / V and nx ny / V.
+template <typename T>
+__global__ void __launch_bounds__(LIN_BLOCK) k_mg_prolong_vec(int nx, int ny, int nz, int cnx,
+                                                              int cny, FastDiv fx, FastDiv fxy,
+                                                              const T* __restrict__ xc,
+                                                              T* __restrict__ xf,
+                                                              const double* skip) {
+    if (skipped(skip)) return;
+    constexpr int V = 16 / (int)sizeof(T);
+    using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    const long long NV = (long long)nx * ny * nz / V;
+    for (long long q = blockIdx.x * (long long)LIN_BLOCK + threadIdx.x; q < NV;
+         q += (long long)gridDim.x * LIN_BLOCK) {
+        int iv, j, k;
+        coords_fd(q, fx, fxy, iv, j, k);
+        const T* pc = xc + (long long)(V / 2) * iv + (long long)cnx * ((j >> 1) + (long long)cny * (k >> 1));
+        VT v = reinterpret_cast<VT*>(xf)[q];
+        if constexpr (sizeof(T) == 4) {
+            const float2 pp = *reinterpret_cast<const float2*>(pc);
+            v.x += pp.x; v.y += pp.x; v.z += pp.y; v.w += pp.y;
+        } else {
+            const double pp = *pc;
+            v.x += pp; v.y += pp;
+        }
+        reinterpret_cast<VT*>(xf)[q] = v;
     }
 }
 
@@ -996,9 +1080,9 @@ cudaError_t LinLaunch::bicg_init(long long N, const double* b, double* r, double
     return end();
 }
 cudaError_t LinLaunch::bicg_p(long long N, const double* scal, const double* r, const double* v,
-                              double* p, int first) {
+                              double* p, int first, double* rh) {
     begin("bicg_update_p");
-    k_bicg_p<<<stream_blocks(N), LIN_BLOCK, 0, st>>>(N, scal, r, v, p, first);
+    k_bicg_p<<<stream_blocks(N), LIN_BLOCK, 0, st>>>(N, scal, r, v, p, first, rh);
     return end();
 }
 cudaError_t LinLaunch::bicg_s(long long N, const double* scal, const double* r, const double* v,
@@ -1035,7 +1119,11 @@ cudaError_t LinLaunch::smooth(const Op<T>& A, const T* b, const T* xin, T* xout,
     B.skip = skip;
     // (FP32 only: the FP64 sweep is bound by its FP64 arithmetic, not by load latency, and
     // its z-marching form measured slower)
-    if (sizeof(T) == 4 && !first && A.nz % ZM == 0 && nxy >= 4 * LIN_BLOCK && xin != xout) {
+    const auto al16 = [](const void* p) { return ((unsigned long long)p & 15ull) == 0; };
+    if (first && (A.N * (long long)sizeof(T)) % 16 == 0 && al16(A.wid) && al16(b) && al16(xout)) {
+        k_mg_smooth_first_vec<T><<<stream_blocks(A.N * (long long)sizeof(T) / 16), LIN_BLOCK, 0, st>>>(
+            A.N, A.wid, b, xout, skip);
+    } else if (sizeof(T) == 4 && !first && A.nz % ZM == 0 && nxy >= 4 * LIN_BLOCK && xin != xout) {
         const dim3 g((unsigned)((nxy + LIN_BLOCK - 1) / LIN_BLOCK), (unsigned)((A.nz + ZM - 1) / ZM));
         k_mg_smooth_zm<T><<<g, LIN_BLOCK, 0, st>>>(B, b, xin, xout, omega);
     } else {
@@ -1066,9 +1154,20 @@ template <typename T>
 cudaError_t LinLaunch::prolong(int nx, int ny, int nz, int cnx, int cny, const T* xc, T* xf) {
     if ((long long)nx * ny * nz == fine_N) begin(sizeof(T) == 4 ? "mg_prolong_f32_fine" : "mg_prolong_f64_fine");
     else begin(sizeof(T) == 4 ? "mg_prolong_f32" : "mg_prolong_f64");
-    k_mg_prolong<T><<<stream_blocks((long long)nx * ny * nz), LIN_BLOCK, 0, st>>>(
-        nx, ny, nz, cnx, cny, make_fastdiv((unsigned)nx), make_fastdiv((unsigned)nx * ny), xc, xf,
-        skip);
+    constexpr int V = 16 / (int)sizeof(T);
+    const long long NV = (long long)nx * ny * nz / V;
+    // the vector form: whole 16-byte groups of fine cells along x, their parents at an offset
+    // of V / 2 per group (cnx = nx / 2 is then a multiple of V / 2), aligned rows
+    if (nx % V == 0 && cnx * 2 == nx && ((unsigned long long)xf & 15ull) == 0 &&
+        ((unsigned long long)xc & (sizeof(T) * V / 2 - 1)) == 0) {
+        k_mg_prolong_vec<T><<<stream_blocks(NV), LIN_BLOCK, 0, st>>>(
+            nx, ny, nz, cnx, cny, make_fastdiv((unsigned)(nx / V)), make_fastdiv((unsigned)(nx / V) * ny),
+            xc, xf, skip);
+    } else {
+        k_mg_prolong<T><<<stream_blocks((long long)nx * ny * nz), LIN_BLOCK, 0, st>>>(
+            nx, ny, nz, cnx, cny, make_fastdiv((unsigned)nx), make_fastdiv((unsigned)nx * ny), xc,
+            xf, skip);
+    }
     return end();
 }
 template <typename TF, typename TC>

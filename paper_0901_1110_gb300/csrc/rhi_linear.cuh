@@ -50,10 +50,15 @@ constexpr long long COARSE_MAX = 8192;
 // x += alpha M^-1 p only) and S_CONT (1 while another iteration follows).
 // S_BEST / S_BESTIT: the smallest r.r so far and its iteration; S_STALL: the loop ended because
 // r.r had not fallen below 0.81 of that best (10% in ||r||) for STALL_ITS iterations.
+// Restarts: S_INNER (0: none) is a relative bound on r.r; once r.r falls below S_INNER times
+// S_RR0, its value at the start or the last restart, or once the solve stagnates, the next
+// iteration restarts from the current x and r with a fresh shadow vector rh = r (S_RST), at
+// most MAX_RESTARTS times (S_NRST counts them).
 enum { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RR, S_BREAK, S_TMP, S_RHO, S_OMEGA, S_SS, S_TS,
-       S_TT, S_RV, S_DONE, S_ITS, S_THR, S_MAXIT, S_HALF, S_CONT, S_BEST, S_BESTIT, S_STALL,
-       S_NSCAL = 24 };
+       S_TT, S_RV, S_DONE, S_ITS, S_THR, S_MAXIT, S_INNER, S_HALF, S_CONT, S_BEST, S_BESTIT,
+       S_STALL, S_RR0, S_NRST, S_RST, S_NSCAL = 32 };
 constexpr int STALL_ITS = 20;
+constexpr int MAX_RESTARTS = 8;
 enum { RED_SUM = 0, RED_ALPHA = 1, RED_BETA = 2, RED_BICG_ALPHA = 3, RED_BICG_OMEGA = 4,
        RED_BICG_RHO = 5, RED_MAX = 6, RED_BICG_START = 7, RED_BICG_SS = 8,
        RED_BICG_NEXT = 9 };
@@ -99,9 +104,10 @@ struct LinLaunch {
                           int two_dots, double* part, int& nparts);
     cudaError_t bicg_init(long long N, const double* b, double* r, double* rh, double* x,
                           double* part, int& nparts);
-    // first: 1 p = r; 0 the update; -1 decided on the device (p = r while S_ITS = 0)
+    // first: 1 p = r; 0 the update; -1 decided on the device (p = r, and rh = r when rh is
+    // given, at S_ITS = 0 or after a restart)
     cudaError_t bicg_p(long long N, const double* scal, const double* r, const double* v,
-                       double* p, int first);
+                       double* p, int first, double* rh = nullptr);
     cudaError_t bicg_s(long long N, const double* scal, const double* r, const double* v,
                        double* s, double* part, int& nparts);
     cudaError_t bicg_xr(long long N, const double* scal, double* x, const double* ph,
