@@ -109,6 +109,9 @@ def alg_bytes(nonsym):
         "cell_residual_schur": 8 * (5 + 5 + 3 + 3 + 1) + 8 * (1 + 1 + 4 + 4),
         "cell_prep_residual_schur": 8 * (4 + 1 + 3 + 3) + 8 * (5 + 1 + 1 + 4 + 4),
         "faces_limiter": 8 * 2 + 8 * 3,
+        # a trial iterate the Newton loop expects to converge: W alone, then f alone
+        "faces_w": 8 * 2 + 8 * 3,
+        "cell_residual": 8 * (5 + 5 + 3 + 3 + 1),
         "update_recover_limit": 8 * (5 + 1 + 1 + 1 + 4 + 4) + 8 * (5 + 1),
         "cg_matvec_dot": 8 * (1 + 3 + 1) + 8,
         "cg_update_xr": 8 * 4 + 8 * 2,
@@ -371,7 +374,8 @@ def run_form(rhi, w, torch, steps, warmup, precond, ab, limiter_jacobian=0, max_
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     agg = dict(newton_its=0, pcg_its=0, vcycles=0, launches=0, backtracks=0, learned_used=0,
-               guess_restarts=0, host_syncs=0, krylov_fallbacks=0, krylov_stalls=0)
+               guess_restarts=0, host_syncs=0, krylov_fallbacks=0, krylov_stalls=0,
+               final_predicted=0, final_missed=0)
     e0.record(stream)
     hist, res0, prev0 = [], [], []
     agg["newton_per_step"], agg["krylov_per_step"] = [], []
@@ -576,11 +580,32 @@ def e2e_form(rhi, w, torch, steps, warmup, precond, limiter_jacobian=0, max_newt
     if weights is not None:
         s.mlp_set_weights(weights)
     N = w.N
-    pin = lambda m: torch.empty(m, dtype=torch.float64, pin_memory=True).numpy()
+    pinned = []
+
+    def pin(m):
+        t = torch.empty(m, dtype=torch.float64, pin_memory=True)
+        pinned.append(t)
+        return t.numpy()
     st = w.state()
     E, e, n, nH = pin(N), pin(N), pin(w.ns * N), pin(N)
     E[:] = st["E"]; e[:] = st["e"]; n[:] = st["n"].ravel(); nH[:] = w.nH.ravel()
     oE, oe, on = pin(N), pin(N), pin(w.ns * N)
+    # the host link's rate into and out of these pinned buffers, by torch's own copies of the
+    # state's bytes (best of three), beside which the library's copies are read
+    outs = pinned[4:7]                                   # oE, oe, on
+    devs = [torch.empty_like(t, device="cuda") for t in outs]
+    rates = {}
+    for name in ("d2h", "h2d"):
+        best = float("inf")
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            for hb, db in zip(outs, devs):
+                (hb.copy_(db, non_blocking=True) if name == "d2h" else db.copy_(hb, non_blocking=True))
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t)
+        rates[name] = sum(d.numel() for d in devs) * 8 / best / 1e9
+    del devs
     # the same step indices as the device-timed region: warm-up steps first, untimed
     for _ in range(warmup):
         s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol)
@@ -612,7 +637,7 @@ def e2e_form(rhi, w, torch, steps, warmup, precond, limiter_jacobian=0, max_newt
     s.close()
     h2d = 8 * N * (3 + w.ns) + 20 * len(w.src_rate)
     d2h = 8 * N * (2 + w.ns)
-    return N * steps / dt, h2d, d2h, {k: 1e3 * v / steps for k, v in split.items()}
+    return N * steps / dt, h2d, d2h, {k: 1e3 * v / steps for k, v in split.items()}, rates
 
 
 def main():
@@ -783,11 +808,14 @@ def main():
     if rank == 0:
         if not args.no_e2e:
             pc, guess = FORMS[order[-1]]
-            e2e_val, h2d, d2h, split = e2e_form(rhi, w, torch, args.steps, args.warmup, pc,
-                                                args.limiter_jacobian, args.max_newton, guess,
-                                                weights if guess == rhi.RHI_GUESS_LEARNED else None)
+            e2e_val, h2d, d2h, split, rates = e2e_form(
+                rhi, w, torch, args.steps, args.warmup, pc, args.limiter_jacobian,
+                args.max_newton, guess, weights if guess == rhi.RHI_GUESS_LEARNED else None)
             line["e2e"] = {"value": world * e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                           "d2h_bytes_per_step": d2h, "wall_ms_per_step": split}
+                           "d2h_bytes_per_step": d2h, "wall_ms_per_step": split,
+                           "host_link_gbs": rates,
+                           "get_state_gbs": d2h / (split["get_state"] * 1e-3) / 1e9,
+                           "set_state_gbs": (h2d - 20 * len(w.src_rate)) / (split["set_state"] * 1e-3) / 1e9}
         if not args.no_cpu_baseline:
             line["cpu_baseline"], (wsub, refs) = cpu_baseline_sample()
             line["error_vs_oracle"] = {

@@ -115,6 +115,12 @@ typedef struct {
                                non-symmetric 7-point matrix, whose coarse levels then carry
                                both couplings of each face); 0 the lagged-D matrix
                                (symmetric), as a preconditioner of the Newton matrix        */
+    int predict_final;      /* 1: when the last two Newton residuals predict (quadratic
+                               model, with a factor 10 of margin) that the full step ends the
+                               iteration, its trial iterate is evaluated for f alone (no
+                               Jacobian, no Schur system); if ||f|| is then not below the
+                               tolerance, the iterate is evaluated again in full.  The
+                               iterates and residuals are those of 0 (no prediction)         */
     double krylov_restart;  /* BiCGStab restarts (shadow residual set to the current residual)
                                each time ||r|| has fallen below this fraction of its value at
                                the last start; 0: only on stagnation (||r|| not 10% below its
@@ -151,6 +157,8 @@ typedef struct {
                                Krylov results, the final wait)                               */
     int krylov_stalls;      /* BiCGStab solves ended because ||r|| had not fallen by 10% in 20
                                iterations (the Newton step then uses that inexact solution)  */
+    int final_predicted;    /* predict_final: trial iterates evaluated for f alone ...       */
+    int final_missed;       /* ... of which did not converge and were evaluated again        */
     double res_initial;     /* ||f(U_0)|| (eq. rmsnorm, scaled)                              */
     double res_final;       /* ||f(U^{n+1})||                                                */
     double res_guess_prev;  /* ||f(U^n)|| when a learned guess was tried, else 0             */
@@ -166,7 +174,7 @@ typedef struct rhi_ctx* rhi_handle;
    (limiter_jacobian 0), tau 0.99, lam_min 1/16, growth_max 1e3, watchdog 3, max_newton 50,
    max_pcg 200, previous-step guess, FP64 multigrid with 6 levels, 2 + 2 sweeps, 16 coarse
    sweeps, omega 0.9, V-cycle graph on, BiCGStab graph on, multigrid of the Newton matrix
-   (mg_matrix 1), krylov_restart -1 (0.01 with the FP32 multigrid, else 0),
+   (mg_matrix 1), predict_final 1, krylov_restart -1 (0.01 with the FP32 multigrid, else 0),
    learned-guess gates mlp_gate 1e-3, mlp_ood 6,
    mlp_restart 12, mlp_retry 4, fixed steps (dt_norm 0) with tau_tol 0.01, scalings 1,
    kappa_floor 1e-40, mu 0.6, and the grey constants of 13.6 eV monochromatic radiation with a

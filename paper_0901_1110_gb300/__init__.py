@@ -38,7 +38,8 @@ class rhi_params(C.Structure):
                 ("max_newton", C.c_int), ("max_pcg", C.c_int), ("guess", C.c_int),
                 ("precond", C.c_int), ("mg_levels", C.c_int), ("mg_pre", C.c_int),
                 ("mg_post", C.c_int), ("mg_coarse_sweeps", C.c_int), ("mg_omega", C.c_double), ("vcycle_graph", C.c_int),
-                ("krylov_graph", C.c_int), ("mg_matrix", C.c_int), ("krylov_restart", C.c_double),
+                ("krylov_graph", C.c_int), ("mg_matrix", C.c_int), ("predict_final", C.c_int),
+                ("krylov_restart", C.c_double),
                 ("dt_norm", C.c_int), ("dt_tau_tol", C.c_double), ("model", C.c_int),
                 ("kappa_total", C.c_double), ("kappa_planck", C.c_double), ("mu", C.c_double),
                 ("sk", C.c_double * 3), ("pgam", C.c_double * 3), ("ph", C.c_double * 3),
@@ -49,6 +50,7 @@ class rhi_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("newton_its", C.c_int), ("pcg_its", C.c_int),
                 ("vcycles", C.c_int), ("backtracks", C.c_int), ("lam_min_steps", C.c_int),
                 ("guess_used", C.c_int), ("launches", C.c_int), ("guess_restarts", C.c_int), ("krylov_fallbacks", C.c_int), ("host_syncs", C.c_int), ("krylov_stalls", C.c_int),
+                ("final_predicted", C.c_int), ("final_missed", C.c_int),
                 ("res_initial", C.c_double),
                 ("res_final", C.c_double), ("res_guess_prev", C.c_double), ("ms", C.c_double),
                 ("eps_loc", C.c_double), ("dt_next", C.c_double),

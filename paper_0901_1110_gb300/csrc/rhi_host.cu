@@ -829,6 +829,7 @@ PhysBuffers state_buffers(rhi_ctx* h) {
 int cell(rhi_ctx* h, const StepParams& P, int mode, PhysBuffers B) {
     const int nb = (int)((h->N + cell_block_size() - 1) / cell_block_size());
     Scope s(h->prof, mode == MODE_ITER ? "cell_residual_schur" :
+                     mode == MODE_RESID ? "cell_residual" :
                      (mode == MODE_PREP ? "cell_prep_residual_schur" : "cell_prep_predictor"));
     CK(launch_cell(P, h->ns, mode, B, nb, h->st));
     return RHI_OK;
@@ -838,6 +839,12 @@ int ncell_blocks(const rhi_ctx* h) { return (int)((h->N + cell_block_size() - 1)
 int faces(rhi_ctx* h, const StepParams& P, const double* E, const double* kap, int b) {
     Scope s(h->prof, "faces_limiter");
     CK(launch_faces(P, E, kap, h->W[b], h->PQ[b], h->Kf[b], h->st));
+    return RHI_OK;
+}
+// W alone (an iterate evaluated for its residual only)
+int faces_w(rhi_ctx* h, const StepParams& P, const double* E, const double* kap, int b) {
+    Scope s(h->prof, "faces_w");
+    CK(launch_faces_w(P, h->prm.limiter_jacobian, E, kap, h->W[b], h->st));
     return RHI_OK;
 }
 // exact Newton matrix: fold the opacity coupling into Schur set `set` built from buffer b
@@ -906,6 +913,7 @@ int validate_params(const rhi_params* p) {
     if (p->limiter_jacobian < 0 || p->limiter_jacobian > 2) return 0;
     if (p->mg_matrix != 0 && p->mg_matrix != 1) return 0;
     if (!(p->krylov_restart < 1.0)) return 0;
+    if (p->predict_final != 0 && p->predict_final != 1) return 0;
     if (p->krylov_graph != 0 && p->krylov_graph != 1) return 0;
     if (!(p->mg_omega > 0.0 && p->mg_omega <= 1.0)) return 0;
     if (p->vcycle_graph != 0 && p->vcycle_graph != 1) return 0;
@@ -1023,6 +1031,7 @@ int rhi_params_default(rhi_params* p, int n_species) {
     p->vcycle_graph = 1;
     p->mg_matrix = 1;
     p->krylov_restart = -1.0;
+    p->predict_final = 1;
     p->krylov_graph = 1;
     p->dt_norm = 0;
     p->dt_tau_tol = 0.01;
@@ -1471,6 +1480,7 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
     int bad = 0;
     S.res_history[0] = res;
     int k_start = 0;         // iteration at which the current start was taken
+    double res_prev = 0.0;   // ||f|| of the iterate before U_k (0: none since the start)
     while (!(res < newton_tol) && k < h->prm.max_newton) {
         const bool stalled = k - k_start >= 2 && k < RHI_MAX_HISTORY &&
                              res > 0.9 * S.res_history[k - 2];
@@ -1489,6 +1499,7 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
             r_best = res;
             bad = 0;
             k_start = k;
+            res_prev = 0.0;
             S.guess_used = RHI_GUESS_PREVIOUS;
             S.guess_restarts = 1;
             if (res < newton_tol) break;
@@ -1523,36 +1534,64 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
         const double* ec0 = cur < 0 ? nullptr : U_ec(h, cur);
         const double* n0 = cur < 0 ? h->n_s : U_n(h, cur);
         const double* E0 = cur < 0 ? h->E_s : U_E(h, cur);
-        // U_k + min(lam, cap) S_k into buffer t, its faces, residual and Schur set
-        auto trial = [&](double lam, double* rt) -> int {
-            {
-                Scope s(h->prof, "update_recover_limit");
-                CK(launch_update(P, ns, lam, ec0, n0, E0, h->e_s, h->nH, h->x, h->fMt[set],
-                                 h->MiU[set], U_ec(h, t), U_n(h, t), U_E(h, t), h->kap[t], h->st));
-            }
+        // the trial iterate's faces, residual and (unless resid_only) Schur set
+        auto evaluate = [&](double* rt, bool resid_only) -> int {
             int r2;
-            if ((r2 = faces(h, P, U_E(h, t), h->kap[t], t))) return r2;
+            if (resid_only) {
+                if ((r2 = faces_w(h, P, U_E(h, t), h->kap[t], t))) return r2;
+            } else if ((r2 = faces(h, P, U_E(h, t), h->kap[t], t))) {
+                return r2;
+            }
             PhysBuffers C = state_buffers(h);
             C.ec = U_ec(h, t); C.n = U_n(h, t); C.E = U_E(h, t); C.W = h->W[t];
             C.PQ = h->PQ[t]; C.diag_ns = h->diag_ns[1 - set];
             C.diag = h->diag[1 - set]; C.rhs = h->rhs[1 - set];
             C.fMt = h->fMt[1 - set]; C.MiU = h->MiU[1 - set];
-            if ((r2 = cell(h, P, MODE_ITER, C))) return r2;
+            if ((r2 = cell(h, P, resid_only ? MODE_RESID : MODE_ITER, C))) return r2;
             return residual_norm(h, ncell_blocks(h), rt);
         };
+        // U_k + min(lam, cap) S_k into buffer t, then its evaluation
+        auto trial = [&](double lam, double* rt, bool resid_only = false) -> int {
+            {
+                Scope s(h->prof, "update_recover_limit");
+                CK(launch_update(P, ns, lam, ec0, n0, E0, h->e_s, h->nH, h->x, h->fMt[set],
+                                 h->MiU[set], U_ec(h, t), U_n(h, t), U_E(h, t), h->kap[t], h->st));
+            }
+            return evaluate(rt, resid_only);
+        };
+        // The full step is expected to end the iteration when the quadratic model through the
+        // last two residuals, ||f_k+1|| ~ ||f_k||^2 ||f_k|| / ||f_k-1||^2, puts it below a tenth
+        // of the tolerance: its iterate is then evaluated for f alone, and again in full only
+        // if it did not converge (the Jacobian and Schur system of the last iterate are not
+        // needed).
+        bool resid_only = false;
+        if (h->prm.predict_final && k - k_start >= 1 && res_prev > 0.0) {
+            const double q = res / res_prev;
+            resid_only = q * q * res < 0.1 * newton_tol;
+        }
         // watchdog line search (Sec. 3.2, item 2): full steps, non-monotone for at most
         // `watchdog` iterations without a new best ||f||, else Armijo backtracking
         double rt = 0.0;
-        if ((rc = trial(1.0, &rt))) return rc;
+        if ((rc = trial(1.0, &rt, resid_only))) return rc;
         if (deferred) {
             // the full step's residual read also brought the Krylov solve's outcome back
             rc = bicg_outcome(h, &its);
             if (rc == RHI_ERR_NONPHYSICAL) {
                 if ((rc = krylov_fallback())) { S.status = rc; return rc; }
-                if ((rc = trial(1.0, &rt))) return rc;
+                if ((rc = trial(1.0, &rt))) return rc;        // in full
+                resid_only = false;
             } else if (rc) {
                 S.status = rc;
                 return rc;
+            }
+        }
+        if (resid_only) {
+            S.final_predicted += 1;
+            if (!(rt < newton_tol)) {
+                // not converged after all: the same iterate in full (its residual again, the
+                // Jacobian and the Schur system for the next Newton iteration)
+                S.final_missed += 1;
+                if ((rc = evaluate(&rt, false))) return rc;
             }
         }
         S.pcg_its += its;
@@ -1574,6 +1613,7 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
         }
         cur = t;
         set = 1 - set;
+        res_prev = res;
         res = rt;
         ++k;
         if (k < RHI_MAX_HISTORY) S.res_history[k] = res;

@@ -157,12 +157,16 @@ struct PhysBuffers {
     double* U0;             // optional predictor output (ns + 2) * N
 };
 
-enum CellMode { MODE_PREP = 0, MODE_ITER = 1, MODE_PREP_PREDICT = 2 };
+enum CellMode { MODE_PREP = 0, MODE_ITER = 1, MODE_PREP_PREDICT = 2, MODE_RESID = 3 };
 
 cudaError_t launch_kappa(const StepParams& P, int ns, const double* n, double* kap,
                          cudaStream_t st);
 cudaError_t launch_faces(const StepParams& P, const double* E, const double* kap, double* W,
                          double* PQ, double* K, cudaStream_t st);
+// the face coefficients W alone, with the arithmetic of launch_faces for Newton matrix jm
+// (limiter_jacobian), so that W is the same to the bit
+cudaError_t launch_faces_w(const StepParams& P, int jm, const double* E, const double* kap,
+                           double* W, cudaStream_t st);
 cudaError_t launch_schur_kappa(const StepParams& P, int ns, const double* K, const double* fMt,
                                const double* MiU, double* PQ, double* diag_ns, double* rhs,
                                cudaStream_t st);

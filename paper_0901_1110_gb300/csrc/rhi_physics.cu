@@ -70,7 +70,7 @@ __device__ __forceinline__ void faint_rescale(double& s, double& dE) {
     }
 }
 
-template <int JM>
+template <int JM, bool WONLY = false>
 __device__ __forceinline__ FaceCoef face_coef(const StepParams& P, double Ea, double Eb,
                                               double ka, double kb) {
     constexpr bool PQ = JM >= 1;
@@ -95,6 +95,10 @@ __device__ __forceinline__ FaceCoef face_coef(const StepParams& P, double Ea, do
         }
         const double iden = 1.0 / den;
         r.W = num * iden * P.inv_a2dx2;
+        if (WONLY) {
+            r.P = r.Q = r.W;
+            return r;
+        }
         if (JM == 2)
             r.K = -0.5 * C_LIGHT * s * s * (12.0 * ks * ks + 12.0 * ks * q + q * q) * iden * iden *
                   P.inv_a2dx2 * dE;
@@ -151,12 +155,14 @@ __device__ __forceinline__ BoundaryFace boundary_face(const StepParams& P, doubl
     return r;
 }
 
-template <int JM>
+// WONLY: the coefficients W alone (a trial iterate evaluated for its residual only), by the
+// same arithmetic as the JM kernel's W
+template <int JM, bool WONLY = false>
 __global__ void __launch_bounds__(256) k_faces(const StepParams P, const double* __restrict__ E,
                                                const double* __restrict__ kap,
                                                double* __restrict__ W, double* __restrict__ PQv,
                                                double* __restrict__ Kv) {
-    constexpr bool PQ = JM >= 1;
+    constexpr bool PQ = JM >= 1 && !WONLY;
     const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (c >= P.N) return;
     int i, j, k;
@@ -166,13 +172,13 @@ __global__ void __launch_bounds__(256) k_faces(const StepParams P, const double*
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         FaceCoef f{0.0, 0.0, 0.0, 0.0};
-        if (b.has_lo[ax]) f = face_coef<JM>(P, E[b.lo[ax]], Ec, kap[b.lo[ax]], kc);
+        if (b.has_lo[ax]) f = face_coef<JM, WONLY>(P, E[b.lo[ax]], Ec, kap[b.lo[ax]], kc);
         W[ax * P.N + c] = f.W;
         if (PQ) {
             PQv[ax * P.N + c] = f.P;
             PQv[(3 + ax) * P.N + c] = f.Q;
         }
-        if (JM == 2) Kv[ax * P.N + c] = f.K;
+        if (JM == 2 && !WONLY) Kv[ax * P.N + c] = f.K;
     }
 }
 
@@ -183,6 +189,16 @@ cudaError_t launch_faces(const StepParams& P, const double* E, const double* kap
     if (PQ && K) k_faces<2><<<g, b, 0, st>>>(P, E, kap, W, PQ, K);
     else if (PQ) k_faces<1><<<g, b, 0, st>>>(P, E, kap, W, PQ, nullptr);
     else k_faces<0><<<g, b, 0, st>>>(P, E, kap, W, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_faces_w(const StepParams& P, int jm, const double* E, const double* kap,
+                           double* W, cudaStream_t st) {
+    const int b = 256;
+    const unsigned g = (unsigned)((P.N + b - 1) / b);
+    if (jm == 0) k_faces<0><<<g, b, 0, st>>>(P, E, kap, W, nullptr, nullptr);
+    else if (jm == 1) k_faces<1, true><<<g, b, 0, st>>>(P, E, kap, W, nullptr, nullptr);
+    else k_faces<2, true><<<g, b, 0, st>>>(P, E, kap, W, nullptr, nullptr);
     return cudaGetLastError();
 }
 
@@ -489,6 +505,7 @@ __device__ __forceinline__ void lu_solve2(double (&A)[NM][NM], double (&y)[NM], 
 //                    and the Schur system at U^n.
 // MODE_ITER:         U given; reads g; writes f(U) and the Schur system at U.
 // MODE_PREP_PREDICT: writes g^n and the explicit predictor U^n - dt L(U^n) (capped).
+// MODE_RESID:        U given; reads g; writes f(U) only (the same arithmetic as MODE_ITER).
 
 template <int NS, int MODE>
 __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const PhysBuffers B) {
@@ -500,7 +517,8 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const P
         int i, j, k;
         cell_coords(P, c, i, j, k);
         const Nbr nb = neighbours(P, c, i, j, k);
-        const bool prep = (MODE != MODE_ITER);
+        const bool prep = (MODE != MODE_ITER && MODE != MODE_RESID);
+        constexpr bool JAC = MODE != MODE_PREP_PREDICT && MODE != MODE_RESID;
         const double* En = prep ? B.E_n : B.E;
         const double* nn = prep ? B.n_n : B.n;
         const double E = En[c];
@@ -520,7 +538,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const P
             const double whi = nb.has_hi[ax] ? B.W[ax * N + nb.hi[ax]] : 0.0;
             Dterm += wlo * (E - En[nb.lo[ax]]) + whi * (E - En[nb.hi[ax]]);
             Wsum += wlo + whi;
-            if (MODE != MODE_PREP_PREDICT && B.PQ) {
+            if (JAC && B.PQ) {
                 PQsum += B.PQ[ax * N + c];
                 if (nb.has_hi[ax]) PQsum += B.PQ[(3 + ax) * N + nb.hi[ax]];
             }
@@ -554,8 +572,8 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const P
         }
 
         Local<NS> lo;
-        local_model<NS, MODE != MODE_PREP_PREDICT>(P, ec, n, E, eh, nH, src, Tfix, lo);
-        if constexpr (NS > 0 && MODE != MODE_PREP_PREDICT) {
+        local_model<NS, JAC>(P, ec, n, E, eh, nH, src, Tfix, lo);
+        if constexpr (NS > 0 && JAC) {
             // exact matrix: a Dirichlet face's opacity is the cell's, so its kappa derivative
             // joins the cell's own E-row species entries
             if (P.limiter_newton == 2 && kb_term != 0.0) {
@@ -619,6 +637,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const P
                 fsq += fs[v] * fs[v];
                 if (B.f_out) B.f_out[v * N + c] = fs[v];
             }
+            if constexpr (MODE != MODE_RESID) {
             // scaled local blocks (eq. schur_components); dt theta u_s / u_r products per step
             double M[NM][NM], y[NM], z[NM], Lr[NM];
 #pragma unroll
@@ -645,6 +664,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(const StepParams P, const P
                 B.fMt[r * N + c] = y[r];
                 B.MiU[r * N + c] = z[r];
             }
+            }
         }
     }
     if (MODE != MODE_PREP_PREDICT) {
@@ -659,14 +679,17 @@ cudaError_t launch_cell(const StepParams& P, int ns, int mode, const PhysBuffers
     if (ns == 0) {
         if (mode == MODE_PREP) k_cell<0, MODE_PREP><<<g, b, 0, st>>>(P, B);
         else if (mode == MODE_ITER) k_cell<0, MODE_ITER><<<g, b, 0, st>>>(P, B);
+        else if (mode == MODE_RESID) k_cell<0, MODE_RESID><<<g, b, 0, st>>>(P, B);
         else k_cell<0, MODE_PREP_PREDICT><<<g, b, 0, st>>>(P, B);
     } else if (ns == 1) {
         if (mode == MODE_PREP) k_cell<1, MODE_PREP><<<g, b, 0, st>>>(P, B);
         else if (mode == MODE_ITER) k_cell<1, MODE_ITER><<<g, b, 0, st>>>(P, B);
+        else if (mode == MODE_RESID) k_cell<1, MODE_RESID><<<g, b, 0, st>>>(P, B);
         else k_cell<1, MODE_PREP_PREDICT><<<g, b, 0, st>>>(P, B);
     } else {
         if (mode == MODE_PREP) k_cell<3, MODE_PREP><<<g, b, 0, st>>>(P, B);
         else if (mode == MODE_ITER) k_cell<3, MODE_ITER><<<g, b, 0, st>>>(P, B);
+        else if (mode == MODE_RESID) k_cell<3, MODE_RESID><<<g, b, 0, st>>>(P, B);
         else k_cell<3, MODE_PREP_PREDICT><<<g, b, 0, st>>>(P, B);
     }
     return cudaGetLastError();

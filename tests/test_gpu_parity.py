@@ -327,5 +327,42 @@ def test_krylov_graph_matches_direct_launches(rhi, precond):
             assert a[k] == b[k], (k, a[k], b[k])
     for st in out[1][1]:
         assert st["krylov_fallbacks"] == 0
-        assert st["host_syncs"] <= st["newton_its"] + st["backtracks"] + 2, st
+        assert st["host_syncs"] <= st["newton_its"] + st["backtracks"] + st["final_missed"] + 2, st
         assert st["host_syncs"] < out[0][1][0]["host_syncs"]
+
+
+@pytest.mark.parametrize("precond,tol", [("mg32", 1e-8), ("mg32", TIGHT_NEWTON_TOL),
+                                         ("mg64", 1e-8)])
+def test_predicted_final_iterate_matches_full_evaluation(rhi, precond, tol):
+    """predict_final: the trial iterate the quadratic model expects to end the iteration is
+    evaluated for its residual alone (W only, no Jacobian or Schur system), and in full only
+    when it did not converge.  The iterates are those of predict_final = 0 bit for bit, with
+    the same counts; the residual-only kernels evaluate the same formulas for W and f, which
+    the compiler may contract into FMAs differently (a product that the full kernels reuse),
+    so the last ||f|| of a step agrees to rounding.  At least one prediction is made."""
+    w = WL["lognormal_hhe"]
+    code = {"mg32": rhi.RHI_PRECOND_MG_FP32, "mg64": rhi.RHI_PRECOND_MG_FP64}[precond]
+    out = []
+    for pf in (0, 1):
+        s = rhi.solver_for_workload(w, precond=code, mg_levels=4, limiter_jacobian=2,
+                                    predict_final=pf)
+        stats = []
+        for dt in (w.dt, w.dt, 0.5 * w.dt, w.dt):
+            s.step(dt, newton_tol=tol, lin_tol=1e-10)
+            stats.append(s.stats())
+        out.append((s.get_state(), stats))
+        s.close()
+    for key in ("E", "e", "n"):
+        assert np.array_equal(np.asarray(out[0][0][key]), np.asarray(out[1][0][key])), key
+    for a, b in zip(out[0][1], out[1][1]):
+        for k in ("newton_its", "pcg_its", "vcycles", "backtracks"):
+            assert a[k] == b[k], (k, a[k], b[k])
+        assert np.allclose(a["res_history"], b["res_history"], rtol=1e-12, atol=0.0)
+        assert a["res_history"][:a["newton_its"]] == b["res_history"][:b["newton_its"]]
+        assert abs(a["res_final"] - b["res_final"]) <= 1e-12 * a["res_final"]
+        assert a["final_predicted"] == 0
+    pred = sum(st["final_predicted"] for st in out[1][1])
+    missed = sum(st["final_missed"] for st in out[1][1])
+    print(f"{precond}, tol {tol:g}: {pred} predicted final iterates, {missed} missed, "
+          f"Newton its {[st['newton_its'] for st in out[1][1]]}")
+    assert pred >= 1

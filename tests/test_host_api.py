@@ -27,7 +27,7 @@ def test_params_default_match_the_header(rhi, ns):
                   watchdog=3, limiter_jacobian=0, max_newton=50, max_pcg=200,
                   guess=rhi.RHI_GUESS_PREVIOUS, precond=rhi.RHI_PRECOND_MG_FP64, mg_levels=6,
                   mg_pre=2, mg_post=2, mg_coarse_sweeps=16, mg_omega=0.9, vcycle_graph=1,
-                  krylov_graph=1, mg_matrix=1, krylov_restart=-1.0, dt_norm=0, dt_tau_tol=0.01, mu=0.6,
+                  krylov_graph=1, mg_matrix=1, krylov_restart=-1.0, predict_final=1, dt_norm=0, dt_tau_tol=0.01, mu=0.6,
                   model=rhi.RHI_MODEL_LTE if ns == 0 else rhi.RHI_MODEL_IONIZATION)
     for k, v in expect.items():
         assert getattr(p, k) == v, k
@@ -98,7 +98,7 @@ def test_create_rejects_bad_boundaries(rhi):
     dict(guess=9), dict(mlp_gate=-1.0), dict(mlp_retry=-1), dict(precond=7), dict(mg_levels=0),
     dict(mg_pre=0), dict(mg_coarse_sweeps=0), dict(limiter_jacobian=3), dict(mg_omega=1.5),
     dict(vcycle_graph=2), dict(krylov_graph=2), dict(mg_matrix=2), dict(krylov_restart=1.0),
-    dict(krylov_restart=float("nan")), dict(dt_norm=-2), dict(dt_tau_tol=0.0), dict(y_he=-0.1),
+    dict(krylov_restart=float("nan")), dict(predict_final=2), dict(dt_norm=-2), dict(dt_tau_tol=0.0), dict(y_he=-0.1),
     dict(model=1)])                                   # the LTE model needs n_species = 0
 def test_create_rejects_out_of_range_parameters(rhi, tweak):
     with pytest.raises(rhi.RhiError) as e:
