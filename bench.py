@@ -634,6 +634,28 @@ def e2e_form(rhi, w, torch, steps, warmup, precond, limiter_jacobian=0, max_newt
         n, on = on, n
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    # after the timed loop: the device time of get_state's copies right after a step, beside
+    # torch's own copy of the same bytes from device buffers into pinned buffers just after it
+    # (both on the legacy stream); a slow host link slows both, a slow library copy only one
+    def dev_ms(f):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        f()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    def torch_copy():
+        for hb, db in zip(outs, devs):
+            hb.copy_(db, non_blocking=True)
+    devs = [torch.empty_like(t, device="cuda") for t in outs]
+    after = []
+    for _ in range(4):
+        s.step(w.dt, 1.0, 0.0, w.newton_tol, w.lin_tol)
+        after.append((dev_ms(lambda: s.get_state(oE, oe, on)), dev_ms(torch_copy)))
+    del devs
+    rates["after_step_ms"] = {"get_state": [round(a, 2) for a, _ in after],
+                              "torch_copy": [round(b, 2) for _, b in after]}
     s.close()
     h2d = 8 * N * (3 + w.ns) + 20 * len(w.src_rate)
     d2h = 8 * N * (2 + w.ns)
