@@ -435,7 +435,7 @@ def config_128_plain(rhi, torch, limiter_jacobian, max_newton):
             "newton_its": a[:, 0].astype(int).tolist(), "krylov_its": a[:, 1].astype(int).tolist()}
 
 
-def config_cosmo_run(rhi, torch, n, intervals, max_newton):
+def config_cosmo_run(rhi, torch, n, intervals, max_newton, budget_s=600.0):
     """The cosmological configuration (H + He, sigma_ln = 1.5, 256 clustered sources at 512^3,
     flat Lambda-CDM from z = 10 in 100 equal intervals of cosmic time) over its first
     `intervals` intervals, each with (a, adot) at its middle.  The plain FP64 form takes
@@ -443,7 +443,8 @@ def config_cosmo_run(rhi, torch, n, intervals, max_newton):
     time_step_selection with p = 2, tau_tol = 0.05; a failed step is retried at half its
     length), Newton tol 1e-8; the mixed form then takes the same steps, so that the two final
     states differ only by the forms' arithmetic, and is compared with the plain form per
-    element and in the scaled unknowns."""
+    element and in the scaled unknowns.  The plain form stops after the interval in which its
+    wall time passes budget_s; each finished interval is reported on stderr."""
     from paper_0901_1110_gb300 import inputs
     w = inputs.config_cosmo(n, nsrc=max(1, round(256 * (n / 512) ** 3)))
     out, states, seq = {}, {}, []
@@ -459,13 +460,21 @@ def config_cosmo_run(rhi, torch, n, intervals, max_newton):
         stats, failed = [], 0
         if name == "plain_fp64":
             dt = 1e11
+            t_wall = time.perf_counter()
+            done = 0
             for k in range(intervals):
+                if time.perf_counter() - t_wall > budget_s:
+                    break
                 span, a, adot = w.schedule[k]
                 t = 0.0
-                while t < span * (1.0 - 1e-12):
+                while t < span * (1.0 - 1e-12) and time.perf_counter() - t_wall <= 2.0 * budget_s:
                     d = min(dt, span - t)
                     rc = s.step(d, a, adot, w.newton_tol, w.lin_tol, check=False)
                     while rc in (rhi.RHI_ERR_NONCONVERGED, rhi.RHI_ERR_NONPHYSICAL) and d > 1e6:
+                        st = s.stats()
+                        print(f"  step of {d:.3e} s failed ({rc}) after {st['newton_its']} Newton "
+                              f"iterations, ||f|| {st['res_final']:.2e}, {st['ms']:.0f} ms",
+                              file=sys.stderr, flush=True)
                         failed += 1
                         d *= 0.5
                         rc = s.step(d, a, adot, w.newton_tol, w.lin_tol, check=False)
@@ -474,8 +483,16 @@ def config_cosmo_run(rhi, torch, n, intervals, max_newton):
                     st = s.stats()
                     stats.append(st)
                     seq.append((d, a, adot))
+                    print(f"  step {len(stats)}: dt {d:.3e} s, {st['newton_its']} Newton, "
+                          f"{st['pcg_its']} BiCGStab, {st['ms']:.0f} ms", file=sys.stderr, flush=True)
                     t += d
                     dt = max(st["dt_next"], 1e6)
+                if t < span * (1.0 - 1e-12):
+                    break                       # the time budget ended inside this interval
+                done = k + 1
+                print(f"cosmological interval {done}: {len(stats)} steps, "
+                      f"{time.perf_counter() - t_wall:.1f} s", file=sys.stderr, flush=True)
+            intervals = done
         else:
             for d, a, adot in seq:
                 rc = s.step(d, a, adot, w.newton_tol, w.lin_tol, check=False)
