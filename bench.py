@@ -673,6 +673,11 @@ def e2e_form(rhi, w, torch, steps, warmup, precond, limiter_jacobian=0, max_newt
     del devs
     rates["after_step_ms"] = {"get_state": [round(a, 2) for a, _ in after],
                               "torch_copy": [round(b, 2) for _, b in after]}
+    try:                                  # the CUDA runtime(s) this process has mapped
+        with open("/proc/self/maps") as f:
+            rates["cudart_mapped"] = sorted({ln.split()[-1] for ln in f if "libcudart" in ln})
+    except OSError:
+        pass
     s.close()
     h2d = 8 * N * (3 + w.ns) + 20 * len(w.src_rate)
     d2h = 8 * N * (2 + w.ns)
