@@ -168,6 +168,7 @@ struct rhi_ctx {
     cudaStream_t kst = nullptr;           // capture stream
     bool kg_failed = false;
     double* h_ctl = nullptr;              // pinned: S_THR, S_MAXIT, S_INNER of the next solve
+    int* h_kerr = nullptr;                // pinned: the staged multigrid sweep's wait flag
     int host_syncs = 0;                   // blocking device-to-host reads of the last step
     int kg_body_kernels = 0;              // kernels per iteration of the last graph solve
 
@@ -1102,7 +1103,13 @@ int rhi_create(const rhi_grid* grid, const rhi_bc* bc, const rhi_params* params,
     if (!rc) {
         cudaError_t e = cudaMallocHost(&h->h_scal, sizeof(double) * S_NSCAL);
         if (e == cudaSuccess) e = cudaMallocHost(&h->h_ctl, sizeof(double) * 3);
+        if (e == cudaSuccess) e = cudaMallocHost(&h->h_kerr, sizeof(int));
         if (e != cudaSuccess) rc = fail(h, RHI_ERR_CUDA, "cudaMallocHost");
+        if (!rc) {
+            *h->h_kerr = 0;
+            e = linear_kernels_init();
+            if (e != cudaSuccess) rc = fail(h, RHI_ERR_CUDA, std::string("multigrid kernels: ") + cudaGetErrorString(e));
+        }
     }
     if (!rc) {
         std::vector<double2> tab = build_rate_table();
@@ -1129,6 +1136,7 @@ void rhi_destroy(rhi_handle h) {
     h->allocs.clear();
     if (h->h_scal) cudaFreeHost(h->h_scal);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);
+    if (h->h_kerr) cudaFreeHost(h->h_kerr);
     if (h->kst) cudaStreamSynchronize(h->kst);
     for (auto& c : h->kg) if (c.exec) cudaGraphExecDestroy(c.exec);
     if (h->kst) cudaStreamDestroy(h->kst);
@@ -1372,6 +1380,16 @@ int rhi_mlp_guess(rhi_handle h, double dt, double a, double* U0, int on_device) 
     return RHI_OK;
 }
 
+// after the stream work of a call is done: a staged multigrid sweep that gave up waiting on
+// its copies makes the call fail (the flag is cleared for the next call)
+int bulk_wait_check(rhi_ctx* h) {
+    if (!*h->h_kerr) return RHI_OK;
+    *h->h_kerr = 0;
+    CK(bulk_wait_flag_clear(h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return fail(h, RHI_ERR_CUDA, "multigrid: a staged sweep timed out waiting for its copies");
+}
+
 int rhi_precond_apply(rhi_handle h, const double* r, double* z, int on_device) {
     if (!h || !r || !z) return RHI_ERR_ARG;
     if (!h->have_linear) return fail(h, RHI_ERR_STATE, "rhi_precond_apply: call rhi_linearize first");
@@ -1382,9 +1400,10 @@ int rhi_precond_apply(rhi_handle h, const double* r, double* z, int on_device) {
     int rc = precond_apply(h, h->q, &zr, np);
     if (rc) return rc;
     CK(cudaMemcpyAsync(z, zr, N * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st));
+    CK(bulk_wait_flag_read(h->h_kerr, h->st));
     CK(cudaStreamSynchronize(h->st));
     h->prof.resolve();
-    return RHI_OK;
+    return bulk_wait_check(h);
 }
 
 int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double newton_tol,
@@ -1668,6 +1687,7 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
         CK(cudaMemcpyAsync(h->n_s, U_n(h, cur), (size_t)ns * N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
         CK(cudaMemcpyAsync(h->E_s, U_E(h, cur), N * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     }
+    CK(bulk_wait_flag_read(h->h_kerr, h->st));
     CK(cudaEventRecord(h->ev1, h->st));
     CK(cudaEventSynchronize(h->ev1));
     float ms = 0.f;
@@ -1676,6 +1696,7 @@ int rhi_implicit_step(rhi_handle h, double dt, double a, double adot, double new
     S.launches = h->prof.launches - launches0;
     S.host_syncs = h->host_syncs + 1;          // and the final event wait
     h->prof.resolve();
+    if ((rc = bulk_wait_check(h))) { S.status = rc; return rc; }
     return RHI_OK;
 }
 

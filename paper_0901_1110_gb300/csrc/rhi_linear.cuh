@@ -73,6 +73,13 @@ struct LaunchHook {
     virtual ~LaunchHook() {}
 };
 
+// Once per process, before the first multigrid launch: the shared-memory limit of the staged
+// sweep and the address of its wait-timeout flag.
+cudaError_t linear_kernels_init();
+// The staged sweep's wait-timeout flag into *host (pinned), on stream st; and its reset.
+cudaError_t bulk_wait_flag_read(int* host, cudaStream_t st);
+cudaError_t bulk_wait_flag_clear(cudaStream_t st);
+
 struct LinLaunch {
     cudaStream_t st;
     LaunchHook* hook;

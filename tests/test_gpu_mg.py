@@ -33,6 +33,10 @@ CASES = {
     # ragged extents: odd sizes on the coarser levels, 27 cells on the coarsest
     "lognormal_ragged": dict(shape=(18, 20, 24), bc=("zero_flux",) * 6, seed=0, levels=4),
     "lognormal_periodic": dict(shape=(8, 13, 16), bc=("periodic",) * 6, seed=3, levels=3),
+    # rows of 256 cells and 16 planes: the FP32 finest-level sweeps run as the staged
+    # (bulk-copy) kernel
+    "wide_rows": dict(shape=(16, 6, 256), bc=("zero_flux",) * 6, seed=7, levels=3),
+    "wide_rows_periodic": dict(shape=(16, 5, 256), bc=("periodic",) * 6, seed=8, levels=3),
 }
 # FP64: rounding order only; FP32: the cycle in single precision against the FP64 restatement
 TOL = {"fp64": 1e-12, "fp32": 1e-4}
