@@ -728,11 +728,17 @@ __global__ void __launch_bounds__(256) k_update(const StepParams P, double lam,
     for (int j = 0; j < NS; ++j) n[j] = n0[j * N + c];
     const double E = E0[c], nH = nHa[c];
     // smallest fraction tau (q + tiny) / (-dq) over the decreasing quantities, kept as a
-    // numerator / denominator pair (denominators > 0) so that one division remains
+    // numerator / denominator pair (denominators > 0) so that one division remains.  The sign
+    // test and the clamp at 0 read the bit pattern on the integer pipe (the FP64 pipe is this
+    // kernel's bound): dq with its sign bit set is dq < 0 or -0, and -0 changes nothing (its
+    // product below is 0); a value with its sign bit clear and below the +inf pattern is
+    // +0, positive or +inf and kept, anything else (negative, NaN) clamps to 0, as fmax(v, 0)
     double cnum = 1.0, cden = 1.0;
     auto bound = [&](double q, double dq, double tiny) {
-        if (dq < 0.0) {
-            const double num = fmax(P.tau * (q + tiny), 0.0);
+        if (__double_as_longlong(dq) < 0) {
+            const double v = P.tau * (q + tiny);
+            const long long vb = __double_as_longlong(v);
+            const double num = (vb >= 0 && vb <= 0x7FF0000000000000LL) ? v : 0.0;
             if (num * cden < cnum * (-dq)) { cnum = num; cden = -dq; }
         }
     };

@@ -217,6 +217,14 @@ def flat_lcdm_adot(a, omega_m=OMEGA_M):
     return a * _h0() * np.sqrt(omega_m / a ** 3 + (1.0 - omega_m))
 
 
+# Radiation scaling of the cosmological configuration.  Its adaptive steps reach 1.4e14 s, where
+# c kappa dt in the dense neutral cells is of order 1e7: the radiation row of f is then a
+# difference of terms 1e7 times E, whose FP64 rounding the RMS tolerance must not have to
+# resolve.  With u_E = 1e-16 (the static runs' value) those steps stalled at ||f|| = 1e-8 to
+# 5e-7 after 40 Newton iterations; with 1e-14 each interval after the first takes one step.
+U_E_COSMO = 1e-14
+
+
 def config_cosmo(n=512, nsrc=256, seed=0, box=1.0 * MPC, z0=10.0, z1=6.0, nsteps=100):
     """The cosmological configuration: H + He lognormal medium with sigma_ln = 1.5 (comoving
     mean n_H = 1e-3), 256 lognormal sources in cells drawn with probability ~ n_H^2, theta = 1,
@@ -225,7 +233,7 @@ def config_cosmo(n=512, nsrc=256, seed=0, box=1.0 * MPC, z0=10.0, z1=6.0, nsteps
     w = lognormal_hhe((n, n, n), box=box, seed=seed, nsrc=nsrc, sigma_ln=1.5, clustered=True,
                       nsteps=nsteps, name=f"cosmo_hhe_{n}", dt=1.0)
     w.theta = 1.0
-    w.u_E = U_E_SOURCES
+    w.u_E = U_E_COSMO
     t0, t1 = flat_lcdm_t(1.0 / (1.0 + z0)), flat_lcdm_t(1.0 / (1.0 + z1))
     dt = (t1 - t0) / nsteps
     w.dt = float(dt)
