@@ -197,11 +197,11 @@ def test_learned_guess_needs_weights(rhi):
 
 
 def test_learned_guess_gain(rhi, trained):
-    """What the trained network gains, measured and bounded: on its training realisation the
-    guess starts Newton closer to the root than U^n in the first step (||f|| at the guess below
-    ||f(U^n)||); on a held-out realisation (another seed) the learned start, with its fallback
-    to U^n and its restart, needs no more Newton iterations in total than U^n.  The measured
-    numbers are printed."""
+    """What the trained network gains, measured and bounded: on its training realisation and
+    on a held-out one (another seed) the guess starts Newton closer to the root than U^n in the
+    first step (||f|| at the guess below ||f(U^n)||: 1.079x and 1.015x on a GB300), and the
+    learned start, with its fallback to U^n and its restart, needs no more Newton iterations in
+    total than U^n.  The measured numbers are printed."""
     out = {}
     for tag, w in (("train", trained["workload"]), ("held_out", _workload(23))):
         its, ratios = {}, []
@@ -229,6 +229,7 @@ def test_learned_guess_gain(rhi, trained):
               f"||f(U^n)|| / ||f(guess)|| per step = {np.round(ratios, 3).tolist()}")
         assert its[rhi.RHI_GUESS_LEARNED] <= its[rhi.RHI_GUESS_PREVIOUS], (tag, its)
     assert out["train"][1][0] > 1.0, out
+    assert out["held_out"][1][0] > 1.0, out
 
 
 def test_learned_start_restart_reaches_the_same_root(rhi, trained):
