@@ -541,3 +541,32 @@ def test_step_caps_is_the_largest_feasible_fraction(ns_case):
             assert not feasible(c, cap[c] * 1.05), (c, cap[c])
             bound += 1
     assert bound > 0
+
+
+def test_backward_euler_block_of_cooling_gas_turns_singular():
+    """Where radiative cooling falls with temperature, dL_e/de < 0 and the backward-Euler
+    block M = I + theta dt dL/dx of eq. jacobian_submatrices passes through a singular matrix
+    at a finite dt (det M changes sign).  One cell of photoionised H + He at z = 8.5, 10 times
+    the mean comoving density (1331 times that, proper), 2e5 K, x_HI = 1e-3: M is regular at
+    dt = 1e10 and 1e11 s and has changed the sign of its determinant by 1e12 s.  Steps longer
+    than that cell's cooling time therefore cross a singular local elimination, which the
+    cosmological configuration's adaptive steps of up to 1.4e14 s meet."""
+    w = inputs.lognormal_hhe((1, 1, 1), box=inputs.MPC / 512, seed=0, nsrc=0)
+    w.theta = 1.0
+    w.u_E = 1e-14
+    nH = 1e-2
+    w.nH = np.full((1, 1, 1), nH)
+    p = oracle_problem(w)
+    a = 1.0 / 9.5
+    H0 = 70e5 / inputs.MPC
+    adot = a * H0 * np.sqrt(0.3 / a ** 3 + 0.7)
+    y = w.y_he
+    n = np.array([1e-3 * nH, 1e-3 * y * nH, 1e-2 * y * nH])
+    ne = (nH - n[0]) + n[2] + 2.0 * (y * nH - n[1] - n[2])
+    ntot = nH + y * nH + ne
+    e = cl.K_BOLTZ * 2e5 * ntot / ((cl.GAMMA - 1.0) * cl.mass_density(nH, y * nH))
+    U = np.concatenate([[0.0], n, [1e-14]]).reshape(-1, 1)
+    dets = [np.linalg.det(md.local_blocks(p, U, np.array([e]), dt, a, adot)[0][0])
+            for dt in (1e10, 1e11, 1e12, 1e13)]
+    assert dets[0] > 0 and dets[1] > 0, dets
+    assert dets[2] < 0 and dets[3] < 0, dets
