@@ -1,4 +1,5 @@
-"""The bench's byte and flop models and the roofline kernel choice (CPU; no device).
+"""The bench's byte and flop models, the roofline kernel choice and the reference arm's line
+(CPU; no device).
 
 The HBM fractions the bench line reports divide a kernel's algorithmic bytes by its measured
 launch time, and the roofline sits on the largest-share kernel that has a model.  These tests
@@ -63,3 +64,24 @@ def test_workload_sources_keep_the_256_cube_density():
     assert bench.workload_sources(128) == 8
     assert bench.workload_sources(64) == 1
     assert bench.workload_sources(48) == 1
+
+
+def test_reference_arm_prints_the_contract_line(capsys, monkeypatch):
+    """`bench.py --impl reference` times the oracle on a sub-box of the same workload and prints
+    one JSON line with the bench's keys, `impl` = reference, its own CPU baseline and an e2e
+    block without device copies (a tiny sub-box here, to keep the CPU suite short)."""
+    import json
+    import types
+    monkeypatch.setenv("RHI_REF_SAMPLE_N", "8")
+    args = types.SimpleNamespace(steps=1, warmup=0, n=256)
+    bench.reference_arm(args, 0, 1)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == bench.UNIT and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
